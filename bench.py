@@ -1,0 +1,381 @@
+"""Benchmark of the static bucketed hash table path on GB300.
+
+Default workload: the HBM-bound BCHT configuration -- 2^28 unique uint32
+key/value pairs, bucket of 16 pairs, three hash functions; each step builds a
+table at load factor 0.99 and one at 0.9 (2.17 / 2.39 GB, far beyond L2) and
+runs 2^28 all-positive and 2^28 all-negative finds on each. ``value`` is the
+keys processed per second (built + queried), device-timed with inputs
+resident in HBM; ``e2e`` is the same metric through the public API from
+pinned host buffers (copies inside the timed region).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank builds and queries its own independent tables
+(weak scaling, no data-path collective).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gkeys/s build and find (pos/neg) at LF 0.9/0.99, % HBM peak; served p99 latency"
+LFS = (0.99, 0.9)
+SEED = 0x6768740003  # input seed of the HBM-bound BCHT configuration
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--log2n", type=int, default=28, help="keys per table (log2)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile-lanes", type=int, default=0)
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        load = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
+
+
+def bytes_per_key(op: str, p: float, lf: float) -> float:
+    """Algorithmic bytes per key (query/result or pair, 128 B per bucket probe,
+    plus one write-back of the table for inserts)."""
+    if op == "find":
+        return 4 + 4 + 128 * p
+    if op == "insert":
+        return 8 + 128 * p + 8 / lf
+    if op == "fill":
+        return 8 / lf
+    raise ValueError(op)
+
+
+# ------------------------------------------------------------- CPU oracle ---
+
+def oracle_sample(n: int, lfs=LFS):
+    """Time the oracle (as it stands, single-threaded) on n keys per load factor:
+    build, then n positive and n negative finds. Returns (keys, seconds)."""
+    import oracle as O
+    import workloads as W
+    keys, vals = W.make_keys(n, SEED), W.make_values(n, SEED)
+    pos = W.make_queries(keys, n, 1.0, SEED)
+    neg = W.make_negatives(n, n, SEED)
+    k, v, qp, qn = O._u32(keys), O._u32(vals), O._u32(pos), O._u32(neg)
+    total, secs = 0, 0.0
+    for lf in lfs:
+        T = O.Table(O.BCHT, n, lf, seed=SEED)
+        t0 = time.perf_counter()
+        ok = T.build(k, v)
+        T.find(qp)
+        T.find(qn)
+        secs += time.perf_counter() - t0
+        if ok != 1:
+            raise RuntimeError("oracle build failed")
+        total += 3 * n
+    return total, secs
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    n = 1 << 21
+    oracle_sample(1 << 12)  # compile / warm
+    for _ in range(args.warmup):
+        oracle_sample(n)
+    keys = secs = 0
+    for _ in range(args.steps):
+        k, s = oracle_sample(n)
+        keys += k
+        secs += s
+    value = keys / secs / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": config_of(args, sample_n=n), "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+                         "sample": f"BCHT b=16 h=3, {n} keys per load factor {list(LFS)}: build + "
+                                   f"{n} positive + {n} negative finds, sequential C oracle"},
+        "e2e": {"value": value, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_of(args, sample_n=None):
+    c = {"workload": f"bcht_b16_h3_n2^{args.log2n}_lf0.99+0.9_find_pos+neg",
+         "scheme": "BCHT", "bucket_size": 16, "num_hashes": 3, "keys_per_table": 1 << args.log2n,
+         "load_factors": list(LFS), "queries_per_table": 2 << args.log2n, "positive_fractions": [1.0, 0.0],
+         "l2": "inputs larger than L2 (tables 2.2-2.4 GB, key arrays 1 GB)", "input_seed": SEED}
+    if sample_n:
+        c["oracle_sample_keys"] = sample_n
+    return c
+
+
+# ------------------------------------------------------------------- ours ---
+
+def run_ours(args, world, rank, local):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2108_07232_gb300 as G
+    import workloads as W
+    from paper_2108_07232_gb300 import build as B
+
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or not os.path.exists(G.lib_path()):
+        B.build()
+    if world > 1:
+        dist.barrier()
+    n = 1 << args.log2n
+    seed = SEED + rank
+    keys = W.make_keys(n, seed, device=dev)
+    vals = W.make_values(n, seed, device=dev)
+    pos = W.make_queries(keys, n, 1.0, seed)
+    neg = W.make_negatives(n, n, seed, device=dev)
+    out = torch.empty_like(keys)
+    cfg = {}
+    if args.tile_lanes:
+        cfg["tile_lanes"] = args.tile_lanes
+    if args.blocks_per_sm:
+        cfg["blocks_per_sm"] = args.blocks_per_sm
+    tables = {lf: G.HashTable("bcht", n, lf, seed=seed, **cfg) for lf in LFS}
+    torch.cuda.synchronize()
+
+    launches = [0]
+    phase_ms = {f"{op}@{lf}": [] for lf in LFS for op in ("fill", "insert", "find_pos", "find_neg")}
+
+    def step(record: bool):
+        for lf in LFS:
+            t = tables[lf]
+            t.build(keys, vals)
+            st = t.stats()
+            launches[0] += 2 * st["attempts"]
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e2 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            t.find(pos, out)
+            e1.record()
+            t.find(neg, out)
+            e2.record()
+            launches[0] += 2
+            if record:
+                phase_ms[f"fill@{lf}"].append(st["last_fill_ms"])
+                phase_ms[f"insert@{lf}"].append(st["last_insert_ms"])
+                e2.synchronize()
+                phase_ms[f"find_pos@{lf}"].append(e0.elapsed_time(e1))
+                phase_ms[f"find_neg@{lf}"].append(e1.elapsed_time(e2))
+
+    for _ in range(args.warmup):
+        step(False)
+    # kernel phase times (one separate, recorded pass; the timed loop below has no extra syncs)
+    step(True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    launches[0] = 0
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        step(False)
+    ev1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    keys_per_step = len(LFS) * 3 * n
+    value = world * keys_per_step * args.steps / (ms / 1e3) / 1e9
+    gpu_launches = launches[0]
+
+    # probe counts for the algorithmic bytes: one extra counted build/find (untimed)
+    probes = {}
+    for lf in LFS:
+        tc = G.HashTable("bcht", n, lf, seed=seed, count_probes=1, **cfg)
+        tc.build(keys, vals)
+        st = tc.stats()
+        p_ins = st["insert_probes"] / n
+        tc.reset_counters()
+        tc.find(pos, out)
+        p_pos = tc.stats()["find_probes"] / n
+        tc.reset_counters()
+        tc.find(neg, out)
+        p_neg = tc.stats()["find_probes"] / n
+        probes[lf] = {"insert": p_ins, "find_pos": p_pos, "find_neg": p_neg,
+                      "insert_retries": st["insert_retries"] / n}
+        del tc
+
+    peak, peak_src = peaks()
+    kernels = {}
+    for lf in LFS:
+        for op, key, pp in (("fill", "fill", 0.0), ("insert", "insert", probes[lf]["insert"]),
+                            ("find", "find_pos", probes[lf]["find_pos"]),
+                            ("find", "find_neg", probes[lf]["find_neg"])):
+            t_ms = statistics.median(phase_ms[f"{key}@{lf}"])
+            bpk = bytes_per_key(op, pp, lf)
+            gbs = bpk * n / (t_ms / 1e3) / 1e9
+            kernels[f"{key}@{lf}"] = {"ms": round(t_ms, 4), "gkeys_s": round(n / (t_ms / 1e3) / 1e9, 3),
+                                      "bytes_per_key": round(bpk, 2), "achieved_gbs": round(gbs, 1),
+                                      "frac_of_hbm": round(gbs / peak, 4)}
+    dom_name = max((k for k in kernels if not k.startswith("fill")), key=lambda k: kernels[k]["ms"])
+    dom = kernels[dom_name]
+    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": dom["achieved_gbs"], "peak": peak,
+                "unit": "GB/s", "frac": dom["frac_of_hbm"], "traffic": None,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s"}
+
+    # end to end through the public API from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hk, hv = keys.cpu().pin_memory(), vals.cpu().pin_memory()
+        hp, hn = pos.cpu().pin_memory(), neg.cpu().pin_memory()
+        hout = torch.empty_like(hk).pin_memory()
+
+        def host_step():
+            for lf in LFS:
+                t = tables[lf]
+                t.build(hk, hv)
+                t.find(hp, hout)
+                t.find(hn, hout)
+            return int(hout[0])  # the step's result is on the host
+
+        host_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            host_step()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([el], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            el = float(tt.item())
+        e2e = {"value": world * keys_per_step * args.steps / el / 1e9, "unit": "Gkeys/s",
+               "h2d_bytes_per_step": len(LFS) * (8 * n + 8 * n),
+               "d2h_bytes_per_step": len(LFS) * 8 * n,
+               "api": "HashTable.build/find on pinned CPU tensors (ght_build_host / ght_find_host)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ns = 1 << 22
+        keys_done, secs = oracle_sample(ns)
+        cpu = {"value": keys_done / secs / 1e9, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+               "sample": f"BCHT b=16 h=3, {ns} keys per load factor {list(LFS)}: sequential C oracle "
+                         f"build + {ns} positive + {ns} negative finds ({secs:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "Gkeys/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": config_of(args), "roofline": roofline,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clocks,
+            "kernels": kernels, "probes_per_key": probes,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

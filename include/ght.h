@@ -1,0 +1,178 @@
+/*
+ * ght.h -- C ABI of the GB300 (sm_103a) static bucketed GPU hash tables.
+ *
+ * The method is that of Awad, Ashkiani, Porumbescu, Farach-Colton and Owens,
+ * "Better GPU Hash Tables" (arXiv 2108.07232): a static table built once on one
+ * GPU from an unordered array of 32-bit key/value pairs, then queried in bulk
+ * (Section I). Schemes:
+ *   GHT_BCHT     bucketed cuckoo, b = 16, three hash functions (Sec. III-A, V-B)
+ *   GHT_P2BHT    bucketed power of two choices, b = 16 (Sec. III-B, V-C)
+ *   GHT_IHT      iceberg, b = 16, primary + two secondaries, t = 13 (Sec. III-C, V-D)
+ *   GHT_CUCKOO1  bucket size one cuckoo ("1CHT"), three hash functions (Sec. VII)
+ *   GHT_BCHT_LB  load-balanced bucketed cuckoo (Sec. III-A, last paragraph)
+ *
+ * Conventions used by every entry point:
+ *   - Keys and values are uint32. 0xFFFFFFFF (GHT_EMPTY) is the empty key and
+ *     the empty value (Sec. V): it may not be inserted as a key; a find that
+ *     misses, or that queries GHT_EMPTY, returns GHT_EMPTY. A stored value equal
+ *     to GHT_EMPTY cannot be told apart from a miss.
+ *   - Keys passed to one build must be unique (the paper's inputs are unique,
+ *     Sec. VII); duplicates are a precondition violation, not detected.
+ *   - Pointers named d_* are device memory owned by the caller (for example
+ *     torch tensors, int32 reinterpreted as uint32); the library never frees
+ *     them. Pointers named h_* are host memory owned by the caller.
+ *   - Work is issued on the table's stream (ght_set_stream; default: the legacy
+ *     default stream). ght_find is asynchronous; ght_build synchronises the
+ *     stream once per attempt to read the build status.
+ *   - Functions return a ght_status; on error ght_last_error() gives a
+ *     thread-local message. No C++ exception crosses this ABI.
+ *   - The hash family is h_i(k) = ((a_i k + c_i) mod p) mod m, p = 4294967291
+ *     (Sec. VII setup; the paper writes b for c_i). a_i, c_i come from SplitMix64
+ *     seeded with seed XOR (attempt * 0x9E3779B97F4A7C15), drawn a_0, c_0, a_1, ...
+ *     with a_i = 1 + x mod (p-1) and c_i = x mod p.
+ *   - Sizing (Sec. III): m = ceil(capacity / (load_factor * b)) buckets of b
+ *     64-bit slots, slot = (value << 32) | key, empty slot = all ones.
+ */
+#ifndef GHT_H
+#define GHT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GHT_EMPTY 0xFFFFFFFFu
+#define GHT_ABI_VERSION 1
+
+typedef enum {
+  GHT_BCHT = 0,
+  GHT_P2BHT = 1,
+  GHT_IHT = 2,
+  GHT_CUCKOO1 = 3,
+  GHT_BCHT_LB = 4
+} ght_scheme;
+
+typedef enum {
+  GHT_OK = 0,
+  GHT_ERR_INVALID_ARG = 1,     /* bad scheme, size, load factor or pointer */
+  GHT_ERR_OOM = 2,             /* device allocation failed */
+  GHT_ERR_BUILD_FAILED = 3,    /* every attempt hit the chain bound or full buckets */
+  GHT_ERR_SENTINEL_KEY = 4,    /* an input key was 0xFFFFFFFF */
+  GHT_ERR_NOT_BUILT = 5,       /* find on a table without a successful build */
+  GHT_ERR_CUDA = 6,            /* a CUDA runtime call failed */
+  GHT_ERR_DEVICE_TIMEOUT = 7,  /* a bounded device or host wait ran out */
+  GHT_ERR_CAPACITY = 8         /* n larger than the table's capacity */
+} ght_status;
+
+typedef struct ght_table ght_table; /* opaque, library-owned */
+
+/* Optional knobs; zero means "scheme default". */
+typedef struct {
+  int32_t bucket_size;   /* slots per bucket: 16 or 32 for bucketed schemes, 1 for CUCKOO1 */
+  int32_t num_hashes;    /* BCHT/BCHT_LB: 2..4; CUCKOO1: 2..4; P2BHT: 2; IHT: 3 */
+  int32_t threshold;     /* IHT t: the primary takes a key while it would hold
+                            fewer than t keys afterwards (default ceil(0.8 b)) */
+  uint32_t max_chain;    /* cuckoo exchanges per insert before failing (default 1000) */
+  uint32_t max_attempts; /* builds with fresh constants before GHT_ERR_BUILD_FAILED (default 50, Sec. VII) */
+  int32_t count_probes;  /* 1: kernels accumulate probe counters (slower; off for timing) */
+  int32_t tile_lanes;    /* lanes that read one bucket together: 4, 8 or 16 (default 8) */
+  int32_t blocks_per_sm; /* grid = SMs x this; 0 = as many as fit */
+  int32_t reserved[8];
+} ght_config;
+
+typedef struct {
+  int32_t scheme, bucket_size, num_hashes, threshold;
+  uint64_t num_buckets, num_slots, capacity, n_stored;
+  double load_factor;          /* n_stored / num_slots of the last successful build */
+  uint32_t attempts;           /* attempts used by the last build */
+  uint32_t max_chain;
+  uint32_t hash_a[4], hash_c[4];
+  uint64_t insert_probes;      /* bucket reads by inserts, CAS retries excluded (needs count_probes) */
+  uint64_t insert_retries;     /* bucket re-reads after a failed CAS */
+  uint64_t insert_evictions;   /* cuckoo exchanges */
+  uint64_t longest_chain;      /* most exchanges one insert made (needs count_probes) */
+  uint64_t find_probes;        /* bucket reads by finds since the last reset */
+  uint64_t find_queries;       /* queries answered since the last reset */
+  uint64_t table_bytes;        /* device bytes of the table (control block + slots) */
+  int32_t built;
+  int32_t tile_lanes;
+  /* device time of the last successful build's fill and insert kernels and
+   * of the last find kernel, from events on the table's stream (-1 if not
+   * yet complete) */
+  double last_fill_ms, last_insert_ms, last_find_ms;
+} ght_stats_t;
+
+/* Library version string; never NULL. */
+const char *ght_version(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *ght_last_error(void);
+
+/* Fill *out with the defaults of `scheme`. */
+int ght_default_config(int scheme, ght_config *out);
+
+/* Device bytes a table of this shape needs (control block + slots), or 0 if
+ * the arguments are invalid. Lets callers supply their own storage. */
+uint64_t ght_table_bytes(int scheme, uint64_t capacity, double load_factor, const ght_config *cfg);
+
+/* Create an empty table sized for `capacity` keys at `load_factor` in (0, 1]
+ * (Sec. III sizing), with hash constants derived from `seed`. Storage is
+ * allocated on the current device. Returns NULL on error (see ght_last_error). */
+ght_table *ght_create(int scheme, uint64_t capacity, double load_factor, uint64_t seed);
+
+/* As ght_create, with optional knobs (cfg may be NULL) and optional caller
+ * storage: if d_storage is non-NULL it must be device memory of at least
+ * ght_table_bytes(...) bytes, 256-byte aligned, owned by the caller and kept
+ * alive until ght_destroy; the library then allocates no device memory. */
+ght_table *ght_create_ex(int scheme, uint64_t capacity, double load_factor, uint64_t seed,
+                         const ght_config *cfg, void *d_storage, uint64_t storage_bytes);
+
+/* Issue all later work on `cuda_stream` (a cudaStream_t; NULL = legacy default). */
+int ght_set_stream(ght_table *t, void *cuda_stream);
+
+/* Bulk build (Sec. III insertion of every key, Sec. V-B..D kernels): fill the
+ * table with empty pairs, insert the n pairs (d_keys[i], d_values[i]), read
+ * the device status; on failure retry with the next attempt's constants, up
+ * to max_attempts. n <= capacity (else GHT_ERR_CAPACITY). n = 0 builds an
+ * empty table. A second build replaces the contents. */
+int ght_build(ght_table *t, const uint32_t *d_keys, const uint32_t *d_values, uint64_t n);
+
+/* Bulk find (Sec. V-B find and its P2BHT/IHT variants): d_out[i] = value of
+ * d_queries[i], or GHT_EMPTY. Asynchronous on the table's stream; d_out may
+ * not alias d_queries. n = 0 is a no-op. GHT_ERR_NOT_BUILT before a
+ * successful build. */
+int ght_find(const ght_table *t, const uint32_t *d_queries, uint32_t *d_out, uint64_t n);
+
+/* As ght_build / ght_find with HOST arrays: the library copies through
+ * pinned staging buffers in chunks, overlapping host<->device copies with
+ * the kernels, and returns when the results are in h_out. */
+int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_values, uint64_t n);
+int ght_find_host(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out, uint64_t n);
+
+/* Fill *out (synchronises the stream when probe counters are on). */
+int ght_stats(const ght_table *t, ght_stats_t *out);
+
+/* Zero the find counters. */
+int ght_reset_counters(ght_table *t);
+
+/* Copy the raw slot array (num_slots pairs, bucket-major) to host memory
+ * h_slots of n_slots >= num_slots entries; synchronous. For validation. */
+int ght_export(const ght_table *t, uint64_t *h_slots, uint64_t n_slots);
+
+/* Bucket indices of each key under each of the table's hash functions,
+ * computed by a device kernel: d_buckets[i * h + j] = h_j(d_keys[i]). */
+int ght_hash_device(const ght_table *t, const uint32_t *d_keys, uint32_t *d_buckets, uint64_t n);
+
+/* The same bucket computation on the host, with explicit constants:
+ * h_out[i] = ((a * h_keys[i] + c) mod p) mod m, for 1 <= m < 2^32. */
+int ght_hash_host(uint32_t a, uint32_t c, uint32_t m, const uint32_t *h_keys, uint32_t *h_out,
+                  uint64_t n);
+
+/* Release the table (and its storage, if library-owned). NULL is a no-op. */
+void ght_destroy(ght_table *t);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -72,15 +72,15 @@ int orc_default_params(int scheme, uint64_t capacity, double lf, uint64_t seed,
   out->scheme = scheme;
   switch (scheme) {
   case ORC_BCHT:    /* b = 16, three hash functions (Sec. VII recommendations) */
-    out->b = 16; out->h = 3; out->max_chain = 128; break;
+    out->b = 16; out->h = 3; out->max_chain = 1000; break;
   case ORC_P2BHT:   /* two choices */
     out->b = 16; out->h = 2; break;
   case ORC_IHT:     /* primary + two secondaries (Sec. III-C); t = ceil(0.8 b) */
     out->b = 16; out->h = 3; out->t = 13; break;
   case ORC_CUCKOO1: /* bucket size one, three hash functions */
-    out->b = 1; out->h = 3; out->max_chain = 512; break;
+    out->b = 1; out->h = 3; out->max_chain = 1000; break;
   case ORC_BCHT_LB:
-    out->b = 16; out->h = 3; out->max_chain = 128; break;
+    out->b = 16; out->h = 3; out->max_chain = 1000; break;
   default:
     return -1;
   }

@@ -1,0 +1,331 @@
+"""ctypes binding of libght.so (argument marshalling only)."""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(HERE, "_build", "libght.so")
+
+EMPTY = 0xFFFFFFFF
+BCHT, P2BHT, IHT, CUCKOO1, BCHT_LB = 0, 1, 2, 3, 4
+SCHEMES = {"bcht": BCHT, "p2bht": P2BHT, "iht": IHT, "cuckoo1": CUCKOO1, "bcht_lb": BCHT_LB}
+
+STATUS = {
+    0: "GHT_OK", 1: "GHT_ERR_INVALID_ARG", 2: "GHT_ERR_OOM", 3: "GHT_ERR_BUILD_FAILED",
+    4: "GHT_ERR_SENTINEL_KEY", 5: "GHT_ERR_NOT_BUILT", 6: "GHT_ERR_CUDA",
+    7: "GHT_ERR_DEVICE_TIMEOUT", 8: "GHT_ERR_CAPACITY",
+}
+
+
+class GhtError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.status = STATUS.get(code, str(code))
+
+
+class GhtConfig(C.Structure):
+    _fields_ = [
+        ("bucket_size", C.c_int32), ("num_hashes", C.c_int32), ("threshold", C.c_int32),
+        ("max_chain", C.c_uint32), ("max_attempts", C.c_uint32), ("count_probes", C.c_int32),
+        ("tile_lanes", C.c_int32), ("blocks_per_sm", C.c_int32), ("reserved", C.c_int32 * 8),
+    ]
+
+
+class GhtStats(C.Structure):
+    _fields_ = [
+        ("scheme", C.c_int32), ("bucket_size", C.c_int32), ("num_hashes", C.c_int32),
+        ("threshold", C.c_int32), ("num_buckets", C.c_uint64), ("num_slots", C.c_uint64),
+        ("capacity", C.c_uint64), ("n_stored", C.c_uint64), ("load_factor", C.c_double),
+        ("attempts", C.c_uint32), ("max_chain", C.c_uint32), ("hash_a", C.c_uint32 * 4),
+        ("hash_c", C.c_uint32 * 4), ("insert_probes", C.c_uint64), ("insert_retries", C.c_uint64),
+        ("insert_evictions", C.c_uint64), ("longest_chain", C.c_uint64), ("find_probes", C.c_uint64), ("find_queries", C.c_uint64),
+        ("table_bytes", C.c_uint64), ("built", C.c_int32), ("tile_lanes", C.c_int32),
+        ("last_fill_ms", C.c_double), ("last_insert_ms", C.c_double), ("last_find_ms", C.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            d[name] = list(v) if hasattr(v, "__len__") else v
+        h = self.num_hashes
+        d["hash_a"], d["hash_c"] = d["hash_a"][:h], d["hash_c"][:h]
+        return d
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load libght.so. Raises if it has not been built (no fallback path)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                raise RuntimeError(
+                    f"{_LIB_PATH} is missing: build it with `python -m paper_2108_07232_gb300.build`")
+            L = C.CDLL(_LIB_PATH)
+            vp, u64, u32, i32 = C.c_void_p, C.c_uint64, C.c_uint32, C.c_int
+            sig = {
+                "ght_version": ([], C.c_char_p),
+                "ght_last_error": ([], C.c_char_p),
+                "ght_default_config": ([i32, C.POINTER(GhtConfig)], i32),
+                "ght_table_bytes": ([i32, u64, C.c_double, C.POINTER(GhtConfig)], u64),
+                "ght_create": ([i32, u64, C.c_double, u64], vp),
+                "ght_create_ex": ([i32, u64, C.c_double, u64, C.POINTER(GhtConfig), vp, u64], vp),
+                "ght_set_stream": ([vp, vp], i32),
+                "ght_build": ([vp, vp, vp, u64], i32),
+                "ght_find": ([vp, vp, vp, u64], i32),
+                "ght_build_host": ([vp, vp, vp, u64], i32),
+                "ght_find_host": ([vp, vp, vp, u64], i32),
+                "ght_stats": ([vp, C.POINTER(GhtStats)], i32),
+                "ght_reset_counters": ([vp], i32),
+                "ght_export": ([vp, vp, u64], i32),
+                "ght_hash_device": ([vp, vp, vp, u64], i32),
+                "ght_hash_host": ([u32, u32, u32, vp, vp, u64], i32),
+                "ght_destroy": ([vp], None),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def _check(rc: int) -> None:
+    if rc != 0:
+        raise GhtError(rc, lib().ght_last_error().decode())
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    return int(x)
+
+
+def _config(cfg) -> GhtConfig | None:
+    if cfg is None or isinstance(cfg, GhtConfig):
+        return cfg
+    c = GhtConfig()
+    for k, v in dict(cfg).items():
+        if v is not None:
+            setattr(c, k, int(v))
+    return c
+
+
+# --- names of the C ABI -------------------------------------------------------
+
+def ght_version() -> str:
+    return lib().ght_version().decode()
+
+
+def ght_last_error() -> str:
+    return lib().ght_last_error().decode()
+
+
+def ght_default_config(scheme: int) -> GhtConfig:
+    c = GhtConfig()
+    _check(lib().ght_default_config(scheme, C.byref(c)))
+    return c
+
+
+def ght_table_bytes(scheme: int, capacity: int, load_factor: float, cfg=None) -> int:
+    c = _config(cfg)
+    return int(lib().ght_table_bytes(scheme, capacity, load_factor, C.byref(c) if c else None))
+
+
+def ght_create(scheme: int, capacity: int, load_factor: float, seed: int) -> int:
+    t = lib().ght_create(scheme, capacity, load_factor, seed)
+    if not t:
+        raise GhtError(1, ght_last_error())
+    return t
+
+
+def ght_create_ex(scheme: int, capacity: int, load_factor: float, seed: int, cfg=None,
+                  d_storage=None, storage_bytes: int = 0) -> int:
+    c = _config(cfg)
+    t = lib().ght_create_ex(scheme, capacity, load_factor, seed, C.byref(c) if c else None,
+                            _ptr(d_storage), storage_bytes)
+    if not t:
+        raise GhtError(1, ght_last_error())
+    return t
+
+
+def ght_set_stream(t: int, stream) -> None:
+    _check(lib().ght_set_stream(t, stream))
+
+
+def ght_build(t: int, d_keys, d_values, n: int) -> None:
+    _check(lib().ght_build(t, _ptr(d_keys), _ptr(d_values), n))
+
+
+def ght_find(t: int, d_queries, d_out, n: int) -> None:
+    _check(lib().ght_find(t, _ptr(d_queries), _ptr(d_out), n))
+
+
+def ght_build_host(t: int, h_keys, h_values, n: int) -> None:
+    _check(lib().ght_build_host(t, _ptr(h_keys), _ptr(h_values), n))
+
+
+def ght_find_host(t: int, h_queries, h_out, n: int) -> None:
+    _check(lib().ght_find_host(t, _ptr(h_queries), _ptr(h_out), n))
+
+
+def ght_stats(t: int) -> GhtStats:
+    s = GhtStats()
+    _check(lib().ght_stats(t, C.byref(s)))
+    return s
+
+
+def ght_reset_counters(t: int) -> None:
+    _check(lib().ght_reset_counters(t))
+
+
+def ght_export(t: int, h_slots, n_slots: int) -> None:
+    _check(lib().ght_export(t, _ptr(h_slots), n_slots))
+
+
+def ght_hash_device(t: int, d_keys, d_buckets, n: int) -> None:
+    _check(lib().ght_hash_device(t, _ptr(d_keys), _ptr(d_buckets), n))
+
+
+def ght_hash_host(a: int, c: int, m: int, h_keys, h_out, n: int) -> None:
+    _check(lib().ght_hash_host(a, c, m, _ptr(h_keys), _ptr(h_out), n))
+
+
+def ght_destroy(t: int) -> None:
+    lib().ght_destroy(t)
+
+
+# --- tensor-level wrapper -----------------------------------------------------
+
+class HashTable:
+    """One static table whose storage is a torch tensor on the current CUDA
+    device. Work follows torch's current stream at each call."""
+
+    def __init__(self, scheme, capacity: int, load_factor: float, seed: int = 0, device=None,
+                 **config):
+        import torch
+
+        self.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+        self.capacity = int(capacity)
+        self.load_factor = float(load_factor)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self._cfg = _config(config) if config else None
+        nbytes = ght_table_bytes(self.scheme, self.capacity, self.load_factor, self._cfg)
+        if nbytes == 0:
+            raise GhtError(1, ght_last_error())
+        # torch's allocator hands out blocks aligned far beyond 256 bytes; the
+        # extra 256 bytes cover any allocator that does not
+        self._storage = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self._storage.data_ptr()
+        aligned = (base + 255) & ~255
+        with torch.cuda.device(self.device):
+            self._t = ght_create_ex(self.scheme, self.capacity, self.load_factor, seed, self._cfg,
+                                    aligned, nbytes)
+        self.nbytes = nbytes
+        self._offset = aligned - base
+
+    def slots_view(self):
+        """The table's slot array as a device int64 tensor (no copy)."""
+        n = ght_stats(self._t).num_slots
+        lo = self._offset + 256
+        return self._storage[lo:lo + n * 8].view(__import__("torch").int64)
+
+    # the table handle is freed with the object
+    def close(self) -> None:
+        if getattr(self, "_t", None):
+            ght_destroy(self._t)
+            self._t = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self):
+        import torch
+        ght_set_stream(self._t, torch.cuda.current_stream(self.device).cuda_stream)
+
+    @staticmethod
+    def _u32(x):
+        import torch
+        if x.dtype not in (torch.int32, torch.uint32):
+            raise TypeError("keys, values and queries must be int32 (uint32 bits) tensors")
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x
+
+    def build(self, keys, values) -> None:
+        k, v = self._u32(keys), self._u32(values)
+        if k.numel() != v.numel():
+            raise ValueError("keys and values differ in length")
+        with _device_of(self.device):
+            self._stream()
+            if k.is_cuda:
+                ght_build(self._t, k, v, k.numel())
+            else:
+                ght_build_host(self._t, k, v, k.numel())
+
+    def find(self, queries, out=None):
+        import torch
+        q = self._u32(queries)
+        if out is None:
+            out = torch.empty_like(q)
+        with _device_of(self.device):
+            self._stream()
+            if q.is_cuda:
+                ght_find(self._t, q, out, q.numel())
+            else:
+                ght_find_host(self._t, q, out, q.numel())
+        return out
+
+    def stats(self) -> dict:
+        with _device_of(self.device):
+            self._stream()
+            return ght_stats(self._t).as_dict()
+
+    def reset_counters(self) -> None:
+        self._stream()
+        ght_reset_counters(self._t)
+
+    def export(self):
+        """Raw slots (num_slots uint64 pairs, bucket-major) as a numpy array."""
+        import numpy as np
+        s = ght_stats(self._t)
+        out = np.empty(s.num_slots, dtype=np.uint64)
+        with _device_of(self.device):
+            self._stream()
+            ght_export(self._t, out, out.size)
+        return out
+
+    def hash_device(self, keys):
+        """(n, h) int64 tensor of bucket indices computed on the device."""
+        import torch
+        k = self._u32(keys)
+        h = ght_stats(self._t).num_hashes
+        out = torch.empty(k.numel() * h, dtype=torch.int32, device=k.device)
+        with _device_of(self.device):
+            self._stream()
+            ght_hash_device(self._t, k, out, k.numel())
+        return (out.to(torch.int64) & 0xFFFFFFFF).view(-1, h)
+
+
+def _device_of(dev):
+    import torch
+    return torch.cuda.device(dev)

@@ -1,0 +1,618 @@
+// ght_api.cu -- host side of the C ABI declared in include/ght.h.
+//
+// Sizing, constant derivation, the build retry loop and the host<->device
+// pipelines live here; all table arithmetic on keys runs in the kernels of
+// kern_bcht.cu / kern_other.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+
+#include "ght.h"
+#include "ght_device.cuh"
+#include "ght_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  return fail(GHT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// SplitMix64 (Steele, Lea, Flood, OOPSLA 2014), used to turn a seed into the
+// randomly generated hash constants of Sec. VII.
+uint64_t splitmix64(uint64_t &state) {
+  state += 0x9E3779B97F4A7C15ull;
+  uint64_t z = state;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Wait for `ev` with a deadline instead of an unbounded synchronize.
+int wait_event(cudaEvent_t ev, double seconds) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (uint64_t spins = 0;; ++spins) {
+    const cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return GHT_OK;
+    if (e != cudaErrorNotReady) return cuda_fail(e, "waiting for the device");
+    if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > seconds)
+      return fail(GHT_ERR_DEVICE_TIMEOUT, "device work did not finish within %.0f s", seconds);
+    if (spins > 1000) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    else std::this_thread::yield();
+  }
+}
+
+double wait_limit_seconds() {
+  const char *s = getenv("GHT_WAIT_TIMEOUT_S");
+  const double v = s ? atof(s) : 0.0;
+  return v > 0.0 ? v : 300.0;
+}
+
+constexpr uint64_t kCtrlBytes = sizeof(ght::Ctrl);
+
+struct Shape {
+  int scheme, b, h, t;
+  uint32_t max_chain, max_attempts;
+  int count_probes, tile_lanes, blocks_per_sm;
+  uint64_t m;
+};
+
+int default_config(int scheme, ght_config *c) {
+  memset(c, 0, sizeof *c);
+  switch (scheme) {
+    case GHT_BCHT: c->bucket_size = 16; c->num_hashes = 3; c->max_chain = 1000; break;
+    case GHT_P2BHT: c->bucket_size = 16; c->num_hashes = 2; break;
+    case GHT_IHT: c->bucket_size = 16; c->num_hashes = 3; c->threshold = 13; break;
+    case GHT_CUCKOO1: c->bucket_size = 1; c->num_hashes = 3; c->max_chain = 1000; break;
+    case GHT_BCHT_LB: c->bucket_size = 16; c->num_hashes = 3; c->max_chain = 1000; break;
+    default: return fail(GHT_ERR_INVALID_ARG, "unknown scheme %d", scheme);
+  }
+  c->max_attempts = 50;
+  c->tile_lanes = scheme == GHT_CUCKOO1 ? 1 : 8;
+  return GHT_OK;
+}
+
+// Resolve a config against the scheme's defaults and validate the shape.
+int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Shape *s) {
+  ght_config d;
+  int rc = default_config(scheme, &d);
+  if (rc) return rc;
+  if (user) {
+    if (user->bucket_size) d.bucket_size = user->bucket_size;
+    if (user->num_hashes) d.num_hashes = user->num_hashes;
+    if (user->max_chain) d.max_chain = user->max_chain;
+    if (user->max_attempts) d.max_attempts = user->max_attempts;
+    if (user->tile_lanes) d.tile_lanes = user->tile_lanes;
+    d.count_probes = user->count_probes;
+    d.blocks_per_sm = user->blocks_per_sm;
+    if (user->threshold) d.threshold = user->threshold;
+    else if (scheme == GHT_IHT) d.threshold = (4 * d.bucket_size + 4) / 5;  // ceil(0.8 b)
+  }
+  if (!(lf > 0.0) || !(lf <= 1.0)) return fail(GHT_ERR_INVALID_ARG, "load factor %g is not in (0, 1]", lf);
+  const int b = d.bucket_size, h = d.num_hashes;
+  if (scheme == GHT_CUCKOO1) {
+    if (b != 1) return fail(GHT_ERR_INVALID_ARG, "CUCKOO1 has bucket size 1");
+    if (h < 2 || h > 4) return fail(GHT_ERR_INVALID_ARG, "CUCKOO1 needs 2..4 hash functions");
+  } else {
+    if (b != 16 && b != 32) return fail(GHT_ERR_INVALID_ARG, "bucket size %d (16 or 32)", b);
+    if (scheme == GHT_P2BHT && h != 2) return fail(GHT_ERR_INVALID_ARG, "P2BHT uses 2 hash functions");
+    if (scheme == GHT_IHT && h != 3) return fail(GHT_ERR_INVALID_ARG, "IHT uses 3 hash functions");
+    if ((scheme == GHT_BCHT || scheme == GHT_BCHT_LB) && (h < 2 || h > 4))
+      return fail(GHT_ERR_INVALID_ARG, "BCHT needs 2..4 hash functions");
+    const bool ok = scheme == GHT_BCHT ? ght::bcht_shape_supported(b, d.tile_lanes)
+                                       : ght::other_shape_supported(scheme, b, d.tile_lanes);
+    if (!ok) return fail(GHT_ERR_INVALID_ARG, "tile of %d lanes unsupported for bucket size %d", d.tile_lanes, b);
+  }
+  if (scheme == GHT_IHT && (d.threshold < 1 || d.threshold > b + 1))
+    return fail(GHT_ERR_INVALID_ARG, "IHT threshold %d outside [1, b+1]", d.threshold);
+  // Sec. III: C = m b, load factor n / C  =>  m = ceil(capacity / (lf b))
+  double want = std::ceil((double)capacity / (lf * (double)b));
+  if (want < 1.0) want = 1.0;
+  if (want > 4294967295.0) return fail(GHT_ERR_INVALID_ARG, "table needs more than 2^32-1 buckets");
+  s->scheme = scheme;
+  s->b = b;
+  s->h = h;
+  s->t = d.threshold;
+  s->max_chain = d.max_chain;
+  s->max_attempts = d.max_attempts ? d.max_attempts : 1;
+  s->count_probes = d.count_probes;
+  s->tile_lanes = d.tile_lanes;
+  s->blocks_per_sm = d.blocks_per_sm;
+  s->m = (uint64_t)want;
+  return GHT_OK;
+}
+
+uint64_t bytes_of(const Shape &s) {
+  const uint64_t slots = s.m * (uint64_t)s.b * 8ull;
+  return kCtrlBytes + ((slots + 255ull) & ~255ull);
+}
+
+}  // namespace
+
+struct ght_table {
+  Shape shape;
+  uint64_t capacity = 0;
+  double lf = 0;
+  uint64_t seed = 0;
+  cudaStream_t stream = nullptr;
+  void *storage = nullptr;
+  uint64_t storage_bytes = 0;
+  bool owns_storage = false;
+  uint64_t *slots = nullptr;
+  ght::Ctrl *ctrl = nullptr;
+  uint32_t a[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
+  uint32_t rng_seed = 1;
+  bool built = false;
+  uint64_t n_stored = 0;
+  uint32_t attempts = 0;
+  ght::Ctrl *h_ctrl = nullptr;  // pinned mirror of the control block
+  cudaEvent_t done = nullptr;
+  cudaEvent_t tev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // fill, fill end, insert end, find, find end
+  bool timed_build = false;
+  mutable bool timed_find = false;
+  mutable uint64_t insert_probes = 0, insert_retries = 0, insert_evictions = 0, longest_chain = 0;
+
+  void derive(uint32_t attempt) {
+    uint64_t st = seed ^ ((uint64_t)attempt * 0x9E3779B97F4A7C15ull);
+    for (int i = 0; i < shape.h; ++i) {
+      const uint64_t x = splitmix64(st), y = splitmix64(st);
+      a[i] = (uint32_t)(1u + x % (uint64_t)(ght::kPrime - 1u));
+      c[i] = (uint32_t)(y % (uint64_t)ght::kPrime);
+    }
+    for (int i = shape.h; i < 4; ++i) a[i] = c[i] = 0;
+    uint64_t r = seed ^ 0x4B45524E454Cull ^ ((uint64_t)attempt << 32);
+    rng_seed = (uint32_t)splitmix64(r) | 1u;
+  }
+
+  ght::TableView view() const {
+    ght::TableView v;
+    v.slots = slots;
+    v.ctrl = ctrl;
+    for (int i = 0; i < 4; ++i) {
+      v.hf.a[i] = a[i];
+      v.hf.c[i] = c[i];
+    }
+    v.hf.mod = ght::make_fastmod((uint32_t)shape.m);
+    v.m = (uint32_t)shape.m;
+    v.h = shape.h;
+    v.t = shape.t;
+    v.max_chain = shape.max_chain;
+    v.rng_seed = rng_seed;
+    // Every bucket visit ends in a stored key, an exchange, or a failed CAS
+    // that fills one more slot for good, so a key needs at most
+    // (max_chain + 1) visits of at most h * (b + 1) reads each.
+    const uint64_t steps = ((uint64_t)shape.max_chain + 2ull) * (uint64_t)shape.h * ((uint64_t)shape.b + 2ull) + 64ull;
+    v.max_steps = (uint32_t)std::min<uint64_t>(steps, 0xFFFFFFF0ull);
+    return v;
+  }
+
+  ght::LaunchOpts opts() const {
+    ght::LaunchOpts o;
+    o.tile_lanes = shape.tile_lanes;
+    o.blocks_per_sm = shape.blocks_per_sm;
+    o.count = shape.count_probes != 0;
+    return o;
+  }
+};
+
+namespace {
+
+cudaError_t launch_insert(const ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n) {
+  const ght::TableView tv = t->view();
+  if (t->shape.scheme == GHT_BCHT) return ght::launch_insert_bcht(t->shape.b, tv, k, v, n, t->opts(), t->stream);
+  return ght::launch_insert_other(t->shape.scheme, t->shape.b, tv, k, v, n, t->opts(), t->stream);
+}
+
+cudaError_t launch_find(const ght_table *t, const uint32_t *q, uint32_t *out, uint64_t n) {
+  const ght::TableView tv = t->view();
+  if (t->shape.scheme == GHT_BCHT) return ght::launch_find_bcht(t->shape.b, tv, q, out, n, t->opts(), t->stream);
+  return ght::launch_find_other(t->shape.scheme, t->shape.b, tv, q, out, n, t->opts(), t->stream);
+}
+
+// Read the control block after the stream's work; bounded wait.
+int read_ctrl(const ght_table *t) {
+  cudaError_t e = cudaMemcpyAsync(t->h_ctrl, t->ctrl, kCtrlBytes, cudaMemcpyDeviceToHost, t->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the control block");
+  e = cudaEventRecord(t->done, t->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "recording an event");
+  return wait_event(t->done, wait_limit_seconds());
+}
+
+// One build from device-resident keys: fill, insert, status; retry with the
+// next attempt's constants on failure.
+int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n, uint32_t first_attempt) {
+  t->built = false;
+  t->n_stored = 0;
+  for (uint32_t attempt = first_attempt; attempt < t->shape.max_attempts; ++attempt) {
+    t->derive(attempt);
+    const ght::TableView tv = t->view();
+    cudaEventRecord(t->tev[0], t->stream);
+    cudaError_t e = ght::launch_fill(tv, t->shape.m * (uint64_t)t->shape.b, t->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launching fill");
+    cudaEventRecord(t->tev[1], t->stream);
+    if (n > 0) {
+      e = launch_insert(t, k, v, n);
+      if (e != cudaSuccess) return cuda_fail(e, "launching insert");
+    }
+    cudaEventRecord(t->tev[2], t->stream);
+    t->timed_build = true;
+    int rc = read_ctrl(t);
+    if (rc) return rc;
+    const uint32_t st = t->h_ctrl->status;
+    t->attempts = attempt + 1;
+    t->insert_probes = t->h_ctrl->insert_probes;
+    t->insert_retries = t->h_ctrl->insert_retries;
+    t->insert_evictions = t->h_ctrl->insert_evictions;
+    t->longest_chain = t->h_ctrl->longest_chain;
+    if (st == 0u) {
+      t->built = true;
+      t->n_stored = n;
+      return GHT_OK;
+    }
+    if (st & ght::kStatusSentinel) return fail(GHT_ERR_SENTINEL_KEY, "an input key is the sentinel 0xFFFFFFFF");
+    if (st & ght::kStatusTimeout) return fail(GHT_ERR_DEVICE_TIMEOUT, "a key exceeded the per-key step bound");
+    if (st & ght::kStatusCorrupt) return fail(GHT_ERR_CUDA, "table corrupt: an evicted key did not hash to its bucket");
+  }
+  return fail(GHT_ERR_BUILD_FAILED, "build failed in %u attempts (chain bound or full buckets)", t->shape.max_attempts);
+}
+
+constexpr uint64_t kChunk = 1ull << 23;  // keys per host<->device pipeline chunk
+
+}  // namespace
+
+extern "C" {
+
+const char *ght_version(void) { return "ght 0.1 (sm_103a)"; }
+
+const char *ght_last_error(void) { return g_err.c_str(); }
+
+int ght_default_config(int scheme, ght_config *out) {
+  if (!out) return fail(GHT_ERR_INVALID_ARG, "out is NULL");
+  return default_config(scheme, out);
+}
+
+uint64_t ght_table_bytes(int scheme, uint64_t capacity, double load_factor, const ght_config *cfg) {
+  Shape s;
+  if (resolve(scheme, capacity, load_factor, cfg, &s)) return 0;
+  return bytes_of(s);
+}
+
+ght_table *ght_create_ex(int scheme, uint64_t capacity, double load_factor, uint64_t seed,
+                         const ght_config *cfg, void *d_storage, uint64_t storage_bytes) {
+  Shape s;
+  if (resolve(scheme, capacity, load_factor, cfg, &s)) return nullptr;
+  const uint64_t need = bytes_of(s);
+  if (d_storage) {
+    if (storage_bytes < need) {
+      fail(GHT_ERR_INVALID_ARG, "storage of %llu bytes, need %llu", (unsigned long long)storage_bytes,
+           (unsigned long long)need);
+      return nullptr;
+    }
+    if (((uintptr_t)d_storage & 255u) != 0u) {
+      fail(GHT_ERR_INVALID_ARG, "storage must be 256-byte aligned");
+      return nullptr;
+    }
+  }
+  ght_table *t = new (std::nothrow) ght_table();
+  if (!t) {
+    fail(GHT_ERR_OOM, "host allocation failed");
+    return nullptr;
+  }
+  t->shape = s;
+  t->capacity = capacity;
+  t->lf = load_factor;
+  t->seed = seed;
+  t->storage_bytes = need;
+  if (d_storage) {
+    t->storage = d_storage;
+  } else {
+    const cudaError_t e = cudaMalloc(&t->storage, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete t;
+      fail(GHT_ERR_OOM, "cudaMalloc of %llu bytes: %s", (unsigned long long)need, cudaGetErrorString(e));
+      return nullptr;
+    }
+    t->owns_storage = true;
+  }
+  t->ctrl = reinterpret_cast<ght::Ctrl *>(t->storage);
+  t->slots = reinterpret_cast<uint64_t *>(reinterpret_cast<char *>(t->storage) + kCtrlBytes);
+  cudaError_t e = cudaMallocHost(reinterpret_cast<void **>(&t->h_ctrl), kCtrlBytes);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->done, cudaEventDisableTiming);
+  for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaEventCreate(&t->tev[i]);
+  if (e != cudaSuccess) {
+    cuda_fail(e, "creating table resources");
+    ght_destroy(t);
+    return nullptr;
+  }
+  memset(t->h_ctrl, 0, kCtrlBytes);
+  t->derive(0);
+  return t;
+}
+
+ght_table *ght_create(int scheme, uint64_t capacity, double load_factor, uint64_t seed) {
+  return ght_create_ex(scheme, capacity, load_factor, seed, nullptr, nullptr, 0);
+}
+
+int ght_set_stream(ght_table *t, void *cuda_stream) {
+  if (!t) return fail(GHT_ERR_INVALID_ARG, "table is NULL");
+  t->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  return GHT_OK;
+}
+
+int ght_build(ght_table *t, const uint32_t *d_keys, const uint32_t *d_values, uint64_t n) {
+  if (!t) return fail(GHT_ERR_INVALID_ARG, "table is NULL");
+  if (n > t->capacity) return fail(GHT_ERR_CAPACITY, "n = %llu exceeds capacity %llu", (unsigned long long)n,
+                                   (unsigned long long)t->capacity);
+  if (n > 0 && (!d_keys || !d_values)) return fail(GHT_ERR_INVALID_ARG, "keys or values is NULL");
+  return build_device(t, d_keys, d_values, n, 0);
+}
+
+int ght_find(const ght_table *t, const uint32_t *d_queries, uint32_t *d_out, uint64_t n) {
+  if (!t) return fail(GHT_ERR_INVALID_ARG, "table is NULL");
+  if (!t->built) return fail(GHT_ERR_NOT_BUILT, "table has no successful build");
+  if (n == 0) return GHT_OK;
+  if (!d_queries || !d_out) return fail(GHT_ERR_INVALID_ARG, "queries or out is NULL");
+  cudaEventRecord(t->tev[3], t->stream);
+  const cudaError_t e = launch_find(t, d_queries, d_out, n);
+  if (e != cudaSuccess) return cuda_fail(e, "launching find");
+  cudaEventRecord(t->tev[4], t->stream);
+  t->timed_find = true;
+  return GHT_OK;
+}
+
+int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_values, uint64_t n) {
+  if (!t) return fail(GHT_ERR_INVALID_ARG, "table is NULL");
+  if (n > t->capacity) return fail(GHT_ERR_CAPACITY, "n = %llu exceeds capacity %llu", (unsigned long long)n,
+                                   (unsigned long long)t->capacity);
+  if (n > 0 && (!h_keys || !h_values)) return fail(GHT_ERR_INVALID_ARG, "keys or values is NULL");
+  if (n == 0) return build_device(t, nullptr, nullptr, 0, 0);
+  // Stage the pairs on the device chunk by chunk on a copy stream while the
+  // first attempt inserts each chunk as soon as it has landed; later
+  // attempts (rare) rebuild from the staged copy.
+  uint32_t *d_buf = nullptr;
+  cudaStream_t copy = nullptr;
+  cudaEvent_t landed[2] = {nullptr, nullptr};
+  int rc = GHT_OK;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&d_buf), 2 * n * sizeof(uint32_t), t->stream);
+  if (e != cudaSuccess) return fail(GHT_ERR_OOM, "staging allocation: %s", cudaGetErrorString(e));
+  uint32_t *d_k = d_buf, *d_v = d_buf + n;
+  if ((e = cudaStreamCreateWithFlags(&copy, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&landed[0], cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&landed[1], cudaEventDisableTiming)) != cudaSuccess) {
+    rc = cuda_fail(e, "creating pipeline resources");
+  }
+  if (rc == GHT_OK) {
+    // the staging buffer is ready once the table stream has allocated it
+    if ((e = cudaEventRecord(landed[0], t->stream)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(copy, landed[0], 0)) != cudaSuccess)
+      rc = cuda_fail(e, "ordering the staging copy");
+  }
+  if (rc == GHT_OK) {
+    t->built = false;
+    t->derive(0);
+    const ght::TableView tv = t->view();
+    if ((e = ght::launch_fill(tv, t->shape.m * (uint64_t)t->shape.b, t->stream)) != cudaSuccess)
+      rc = cuda_fail(e, "launching fill");
+    for (uint64_t off = 0, i = 0; rc == GHT_OK && off < n; off += kChunk, ++i) {
+      const uint64_t len = std::min(kChunk, n - off);
+      cudaEvent_t ev = landed[i & 1];
+      if ((e = cudaMemcpyAsync(d_k + off, h_keys + off, len * 4, cudaMemcpyHostToDevice, copy)) != cudaSuccess ||
+          (e = cudaMemcpyAsync(d_v + off, h_values + off, len * 4, cudaMemcpyHostToDevice, copy)) != cudaSuccess ||
+          (e = cudaEventRecord(ev, copy)) != cudaSuccess || (e = cudaStreamWaitEvent(t->stream, ev, 0)) != cudaSuccess) {
+        rc = cuda_fail(e, "staging keys");
+        break;
+      }
+      if ((e = launch_insert(t, d_k + off, d_v + off, len)) != cudaSuccess) rc = cuda_fail(e, "launching insert");
+    }
+    if (rc == GHT_OK) rc = read_ctrl(t);
+    if (rc == GHT_OK) {
+      const uint32_t st = t->h_ctrl->status;
+      t->attempts = 1;
+      t->insert_probes = t->h_ctrl->insert_probes;
+      t->insert_retries = t->h_ctrl->insert_retries;
+      t->insert_evictions = t->h_ctrl->insert_evictions;
+      t->longest_chain = t->h_ctrl->longest_chain;
+      if (st == 0u) {
+        t->built = true;
+        t->n_stored = n;
+      } else if (st & ght::kStatusSentinel) {
+        rc = fail(GHT_ERR_SENTINEL_KEY, "an input key is the sentinel 0xFFFFFFFF");
+      } else if (st & ght::kStatusTimeout) {
+        rc = fail(GHT_ERR_DEVICE_TIMEOUT, "a key exceeded the per-key step bound");
+      } else if (st & ght::kStatusCorrupt) {
+        rc = fail(GHT_ERR_CUDA, "table corrupt: an evicted key did not hash to its bucket");
+      } else {
+        rc = build_device(t, d_k, d_v, n, 1);
+      }
+    }
+  }
+  cudaFreeAsync(d_buf, t->stream);
+  if (rc == GHT_OK) {
+    e = cudaEventRecord(t->done, t->stream);
+    rc = e == cudaSuccess ? wait_event(t->done, wait_limit_seconds()) : cuda_fail(e, "recording an event");
+  }
+  if (landed[0]) cudaEventDestroy(landed[0]);
+  if (landed[1]) cudaEventDestroy(landed[1]);
+  if (copy) cudaStreamDestroy(copy);
+  return rc;
+}
+
+int ght_find_host(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out, uint64_t n) {
+  if (!t) return fail(GHT_ERR_INVALID_ARG, "table is NULL");
+  if (!t->built) return fail(GHT_ERR_NOT_BUILT, "table has no successful build");
+  if (n == 0) return GHT_OK;
+  if (!h_queries || !h_out) return fail(GHT_ERR_INVALID_ARG, "queries or out is NULL");
+  // Three-stage pipeline over chunks: H2D on one copy stream, find on the
+  // table stream, D2H on a second copy stream (both link directions busy).
+  uint32_t *d_buf = nullptr;
+  cudaStream_t up = nullptr, down = nullptr;
+  const uint64_t nchunks = (n + kChunk - 1) / kChunk;
+  cudaEvent_t evs[8] = {};
+  int rc = GHT_OK;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&d_buf), 2 * n * sizeof(uint32_t), t->stream);
+  if (e != cudaSuccess) return fail(GHT_ERR_OOM, "staging allocation: %s", cudaGetErrorString(e));
+  uint32_t *d_q = d_buf, *d_o = d_buf + n;
+  if ((e = cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking)) != cudaSuccess)
+    rc = cuda_fail(e, "creating pipeline streams");
+  for (int i = 0; rc == GHT_OK && i < 8; ++i)
+    if ((e = cudaEventCreateWithFlags(&evs[i], cudaEventDisableTiming)) != cudaSuccess) rc = cuda_fail(e, "creating events");
+  if (rc == GHT_OK) {
+    if ((e = cudaEventRecord(evs[0], t->stream)) != cudaSuccess || (e = cudaStreamWaitEvent(up, evs[0], 0)) != cudaSuccess)
+      rc = cuda_fail(e, "ordering the staging copy");
+  }
+  // events 0..3: "chunk landed" ring; 4..7: "chunk answered" ring. Reusing an
+  // event is safe because each stream consumes them in order.
+  for (uint64_t i = 0; rc == GHT_OK && i < nchunks; ++i) {
+    const uint64_t off = i * kChunk, len = std::min(kChunk, n - off);
+    cudaEvent_t in = evs[i & 3], fin = evs[4 + (i & 3)];
+    if ((e = cudaMemcpyAsync(d_q + off, h_queries + off, len * 4, cudaMemcpyHostToDevice, up)) != cudaSuccess ||
+        (e = cudaEventRecord(in, up)) != cudaSuccess || (e = cudaStreamWaitEvent(t->stream, in, 0)) != cudaSuccess) {
+      rc = cuda_fail(e, "staging queries");
+      break;
+    }
+    if ((e = launch_find(t, d_q + off, d_o + off, len)) != cudaSuccess) {
+      rc = cuda_fail(e, "launching find");
+      break;
+    }
+    if ((e = cudaEventRecord(fin, t->stream)) != cudaSuccess || (e = cudaStreamWaitEvent(down, fin, 0)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(h_out + off, d_o + off, len * 4, cudaMemcpyDeviceToHost, down)) != cudaSuccess) {
+      rc = cuda_fail(e, "returning results");
+      break;
+    }
+  }
+  if (rc == GHT_OK) {
+    // the table stream frees the buffer after the last read-back
+    if ((e = cudaEventRecord(evs[0], down)) != cudaSuccess || (e = cudaStreamWaitEvent(t->stream, evs[0], 0)) != cudaSuccess)
+      rc = cuda_fail(e, "joining the pipeline");
+  }
+  cudaFreeAsync(d_buf, t->stream);
+  if (rc == GHT_OK) {
+    e = cudaEventRecord(t->done, t->stream);
+    rc = e == cudaSuccess ? wait_event(t->done, wait_limit_seconds()) : cuda_fail(e, "recording an event");
+  } else {
+    cudaStreamSynchronize(up);
+    cudaStreamSynchronize(down);
+  }
+  for (auto ev : evs)
+    if (ev) cudaEventDestroy(ev);
+  if (up) cudaStreamDestroy(up);
+  if (down) cudaStreamDestroy(down);
+  return rc;
+}
+
+int ght_stats(const ght_table *t, ght_stats_t *out) {
+  if (!t || !out) return fail(GHT_ERR_INVALID_ARG, "table or out is NULL");
+  memset(out, 0, sizeof *out);
+  out->scheme = t->shape.scheme;
+  out->bucket_size = t->shape.b;
+  out->num_hashes = t->shape.h;
+  out->threshold = t->shape.t;
+  out->num_buckets = t->shape.m;
+  out->num_slots = t->shape.m * (uint64_t)t->shape.b;
+  out->capacity = t->capacity;
+  out->n_stored = t->n_stored;
+  out->load_factor = out->num_slots ? (double)t->n_stored / (double)out->num_slots : 0.0;
+  out->attempts = t->attempts;
+  out->max_chain = t->shape.max_chain;
+  for (int i = 0; i < 4; ++i) {
+    out->hash_a[i] = t->a[i];
+    out->hash_c[i] = t->c[i];
+  }
+  out->table_bytes = t->storage_bytes;
+  out->built = t->built ? 1 : 0;
+  out->tile_lanes = t->shape.tile_lanes;
+  out->insert_probes = t->insert_probes;
+  out->insert_retries = t->insert_retries;
+  out->insert_evictions = t->insert_evictions;
+  out->longest_chain = t->longest_chain;
+  out->last_fill_ms = out->last_insert_ms = out->last_find_ms = -1.0;
+  float ms = 0.f;
+  if (t->timed_build && cudaEventQuery(t->tev[2]) == cudaSuccess) {
+    if (cudaEventElapsedTime(&ms, t->tev[0], t->tev[1]) == cudaSuccess) out->last_fill_ms = ms;
+    if (cudaEventElapsedTime(&ms, t->tev[1], t->tev[2]) == cudaSuccess) out->last_insert_ms = ms;
+  }
+  if (t->timed_find && cudaEventQuery(t->tev[4]) == cudaSuccess &&
+      cudaEventElapsedTime(&ms, t->tev[3], t->tev[4]) == cudaSuccess)
+    out->last_find_ms = ms;
+  cudaGetLastError();
+  if (t->shape.count_probes) {
+    const int rc = read_ctrl(t);
+    if (rc) return rc;
+    out->find_probes = t->h_ctrl->find_probes;
+    out->find_queries = t->h_ctrl->find_queries;
+  }
+  return GHT_OK;
+}
+
+int ght_reset_counters(ght_table *t) {
+  if (!t) return fail(GHT_ERR_INVALID_ARG, "table is NULL");
+  const cudaError_t e = cudaMemsetAsync(&t->ctrl->find_probes, 0, 2 * sizeof(unsigned long long), t->stream);
+  return e == cudaSuccess ? GHT_OK : cuda_fail(e, "resetting counters");
+}
+
+int ght_export(const ght_table *t, uint64_t *h_slots, uint64_t n_slots) {
+  if (!t || !h_slots) return fail(GHT_ERR_INVALID_ARG, "table or h_slots is NULL");
+  const uint64_t total = t->shape.m * (uint64_t)t->shape.b;
+  if (n_slots < total) return fail(GHT_ERR_INVALID_ARG, "h_slots holds %llu pairs, need %llu",
+                                   (unsigned long long)n_slots, (unsigned long long)total);
+  cudaError_t e = cudaMemcpyAsync(h_slots, t->slots, total * 8ull, cudaMemcpyDeviceToHost, t->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "exporting slots");
+  e = cudaEventRecord(t->done, t->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "recording an event");
+  return wait_event(t->done, wait_limit_seconds());
+}
+
+int ght_hash_device(const ght_table *t, const uint32_t *d_keys, uint32_t *d_buckets, uint64_t n) {
+  if (!t) return fail(GHT_ERR_INVALID_ARG, "table is NULL");
+  if (n == 0) return GHT_OK;
+  if (!d_keys || !d_buckets) return fail(GHT_ERR_INVALID_ARG, "keys or buckets is NULL");
+  const cudaError_t e = ght::launch_hash(t->view(), d_keys, d_buckets, n, t->stream);
+  return e == cudaSuccess ? GHT_OK : cuda_fail(e, "launching hash");
+}
+
+int ght_hash_host(uint32_t a, uint32_t c, uint32_t m, const uint32_t *h_keys, uint32_t *h_out, uint64_t n) {
+  if (m == 0) return fail(GHT_ERR_INVALID_ARG, "m must be at least 1");
+  if (n > 0 && (!h_keys || !h_out)) return fail(GHT_ERR_INVALID_ARG, "keys or out is NULL");
+  ght::HashFamily hf;
+  memset(&hf, 0, sizeof hf);
+  hf.a[0] = a;
+  hf.c[0] = c;
+  hf.mod = ght::make_fastmod(m);
+  for (uint64_t i = 0; i < n; ++i) h_out[i] = ght::bucket_of(hf, 0, h_keys[i]);
+  return GHT_OK;
+}
+
+void ght_destroy(ght_table *t) {
+  if (!t) return;
+  if (t->owns_storage && t->storage) {
+    cudaStreamSynchronize(t->stream);
+    cudaFree(t->storage);
+  }
+  if (t->h_ctrl) cudaFreeHost(t->h_ctrl);
+  if (t->done) cudaEventDestroy(t->done);
+  for (auto ev : t->tev)
+    if (ev) cudaEventDestroy(ev);
+  delete t;
+}
+
+}  // extern "C"

@@ -1,0 +1,77 @@
+// ght_internal.h -- launch layer shared by the host API translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <unordered_map>
+
+#include "ght_device.cuh"
+
+namespace ght {
+
+struct LaunchOpts {
+  int tile_lanes = 8;     // lanes per bucket tile
+  int blocks_per_sm = 0;  // 0 = occupancy limit
+  bool count = false;     // probe counters
+};
+
+constexpr int kThreads = 256;
+
+// Grid for a persistent-style launch: at most as many blocks as are resident
+// at once (SMs x blocks per SM), never more than the work needs.
+template <typename K>
+inline cudaError_t grid_for(K kernel, uint64_t n, int blocks_per_sm, int *blocks_out) {
+  static std::mutex mu;
+  static std::unordered_map<const void *, int> occ_cache;
+  static int sms = 0;
+  std::lock_guard<std::mutex> lock(mu);
+  if (sms == 0) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  int per_sm = blocks_per_sm;
+  if (per_sm <= 0) {
+    auto it = occ_cache.find((const void *)kernel);
+    if (it == occ_cache.end()) {
+      int nb = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kThreads, 0);
+      if (e != cudaSuccess) return e;
+      it = occ_cache.emplace((const void *)kernel, nb > 0 ? nb : 1).first;
+    }
+    per_sm = it->second;
+  }
+  const uint64_t want = (n + kThreads - 1) / kThreads;
+  const uint64_t cap = (uint64_t)sms * (uint64_t)per_sm;
+  *blocks_out = (int)(want < cap ? (want > 0 ? want : 1) : cap);
+  return cudaSuccess;
+}
+
+// Warps of a grid share the input in contiguous slices of this many items.
+inline uint64_t per_warp_of(uint64_t n, int blocks) {
+  const uint64_t warps = (uint64_t)blocks * (kThreads / 32);
+  return (n + warps - 1) / warps;
+}
+
+// kern_bcht.cu
+cudaError_t launch_insert_bcht(int B, const TableView &tv, const uint32_t *k, const uint32_t *v,
+                               uint64_t n, const LaunchOpts &o, cudaStream_t s);
+cudaError_t launch_find_bcht(int B, const TableView &tv, const uint32_t *q, uint32_t *out,
+                             uint64_t n, const LaunchOpts &o, cudaStream_t s);
+bool bcht_shape_supported(int B, int G);
+
+// kern_other.cu
+cudaError_t launch_insert_other(int scheme, int B, const TableView &tv, const uint32_t *k,
+                                const uint32_t *v, uint64_t n, const LaunchOpts &o, cudaStream_t s);
+cudaError_t launch_find_other(int scheme, int B, const TableView &tv, const uint32_t *q,
+                              uint32_t *out, uint64_t n, const LaunchOpts &o, cudaStream_t s);
+bool other_shape_supported(int scheme, int B, int G);
+cudaError_t launch_fill(const TableView &tv, uint64_t num_slots, cudaStream_t s);
+cudaError_t launch_hash(const TableView &tv, const uint32_t *k, uint32_t *out, uint64_t n,
+                        cudaStream_t s);
+
+}  // namespace ght

@@ -1,0 +1,54 @@
+// kern_bcht.cu -- instantiations and launchers of the BCHT kernels for every
+// supported tile shape (bucket of 16 or 32 pairs; 4, 8 or 16 lanes per tile).
+#include "ght_internal.h"
+#include "ght_kernels.cuh"
+
+namespace ght {
+
+template <int B, int G>
+static cudaError_t insert_shape(const TableView &tv, const uint32_t *k, const uint32_t *v,
+                                uint64_t n, const LaunchOpts &o, cudaStream_t s) {
+  auto kern = o.count ? bucketed_insert_kernel<kBCHT, B, G, true> : bucketed_insert_kernel<kBCHT, B, G, false>;
+  int blocks = 0;
+  cudaError_t e = grid_for(kern, n, o.blocks_per_sm, &blocks);
+  if (e != cudaSuccess) return e;
+  kern<<<blocks, kThreads, 0, s>>>(tv, k, v, n, per_warp_of(n, blocks));
+  return cudaGetLastError();
+}
+
+template <int B, int G>
+static cudaError_t find_shape(const TableView &tv, const uint32_t *q, uint32_t *out, uint64_t n,
+                              const LaunchOpts &o, cudaStream_t s) {
+  auto kern = o.count ? bucketed_find_kernel<kBCHT, B, G, true> : bucketed_find_kernel<kBCHT, B, G, false>;
+  int blocks = 0;
+  cudaError_t e = grid_for(kern, n, o.blocks_per_sm, &blocks);
+  if (e != cudaSuccess) return e;
+  kern<<<blocks, kThreads, 0, s>>>(tv, q, out, n, per_warp_of(n, blocks));
+  return cudaGetLastError();
+}
+
+bool bcht_shape_supported(int B, int G) {
+  return (B == 16 && (G == 4 || G == 8 || G == 16)) || (B == 32 && (G == 8 || G == 16));
+}
+
+cudaError_t launch_insert_bcht(int B, const TableView &tv, const uint32_t *k, const uint32_t *v,
+                               uint64_t n, const LaunchOpts &o, cudaStream_t s) {
+  if (B == 16 && o.tile_lanes == 8) return insert_shape<16, 8>(tv, k, v, n, o, s);
+  if (B == 16 && o.tile_lanes == 4) return insert_shape<16, 4>(tv, k, v, n, o, s);
+  if (B == 16 && o.tile_lanes == 16) return insert_shape<16, 16>(tv, k, v, n, o, s);
+  if (B == 32 && o.tile_lanes == 8) return insert_shape<32, 8>(tv, k, v, n, o, s);
+  if (B == 32 && o.tile_lanes == 16) return insert_shape<32, 16>(tv, k, v, n, o, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_find_bcht(int B, const TableView &tv, const uint32_t *q, uint32_t *out,
+                             uint64_t n, const LaunchOpts &o, cudaStream_t s) {
+  if (B == 16 && o.tile_lanes == 8) return find_shape<16, 8>(tv, q, out, n, o, s);
+  if (B == 16 && o.tile_lanes == 4) return find_shape<16, 4>(tv, q, out, n, o, s);
+  if (B == 16 && o.tile_lanes == 16) return find_shape<16, 16>(tv, q, out, n, o, s);
+  if (B == 32 && o.tile_lanes == 8) return find_shape<32, 8>(tv, q, out, n, o, s);
+  if (B == 32 && o.tile_lanes == 16) return find_shape<32, 16>(tv, q, out, n, o, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace ght

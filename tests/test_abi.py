@@ -1,0 +1,111 @@
+"""CPU-side checks of the C-ABI library: it builds, loads, exports every entry
+point include/ght.h declares, and its host-side arithmetic (sizing, the hash
+family with its divide-free remainders) agrees with the oracle. No GPU call."""
+
+import os
+import random
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2108_07232_gb300 import build
+    build.build()
+    import paper_2108_07232_gb300 as G
+    return G
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"\b(ght_[a-z_0-9]+)\s*\(", src))
+    return names
+
+
+def test_every_declared_symbol_is_exported(L):
+    lib = L.lib()
+    declared = _declared()
+    assert {"ght_create", "ght_build", "ght_find", "ght_stats", "ght_destroy"} <= declared
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+
+
+def test_version_and_defaults(L):
+    assert "sm_103a" in L.ght_version()
+    c = L.ght_default_config(L.BCHT)
+    assert (c.bucket_size, c.num_hashes, c.max_chain, c.max_attempts) == (16, 3, 1000, 50)
+    c = L.ght_default_config(L.IHT)
+    assert (c.bucket_size, c.num_hashes, c.threshold) == (16, 3, 13)
+    c = L.ght_default_config(L.CUCKOO1)
+    assert (c.bucket_size, c.num_hashes) == (1, 3)
+    with pytest.raises(L.GhtError):
+        L.ght_default_config(9)
+
+
+@pytest.mark.parametrize("scheme,b", [(0, 16), (1, 16), (2, 16), (3, 1), (4, 16)])
+def test_table_bytes_follow_the_oracle_sizing(L, scheme, b):
+    for n, lf in [(1 << 20, 0.9), (268435456, 0.99), (1000, 0.6), (0, 0.5), (17, 1.0)]:
+        m = O.num_buckets(n, lf, b)
+        slots = m * b * 8
+        assert L.ght_table_bytes(scheme, n, lf) == 256 + ((slots + 255) // 256) * 256
+
+
+def test_table_bytes_rejects_bad_shapes(L):
+    assert L.ght_table_bytes(0, 100, 0.0) == 0
+    assert L.ght_table_bytes(0, 100, 1.01) == 0
+    assert L.ght_table_bytes(0, 100, 0.9, {"bucket_size": 8}) == 0
+    assert L.ght_table_bytes(1, 100, 0.9, {"num_hashes": 3}) == 0
+    assert L.ght_table_bytes(3, 2**40, 0.5) == 0
+    assert L.ght_table_bytes(0, 100, 0.9, {"tile_lanes": 2}) == 0
+    assert L.ght_table_bytes(0, 100, 0.9, {"bucket_size": 32, "tile_lanes": 4}) == 0
+    assert L.ght_table_bytes(2, 100, 0.9, {"bucket_size": 32}) > 0  # IHT b = 32, t = 26
+
+
+def _host_hash(L, a, c, m, keys):
+    keys = np.ascontiguousarray(keys, dtype=np.uint32)
+    out = np.empty_like(keys)
+    L.ght_hash_host(a, c, m, keys, out, keys.size)
+    return out
+
+
+def test_host_hash_matches_golden_vectors(L, golden_dir):
+    for line in open(os.path.join(golden_dir, "hash_vectors.txt")):
+        body = line.split("#", 1)[0].split()
+        if body:
+            a, c, m, k, want = map(int, body)
+            assert _host_hash(L, a, c, m, [k])[0] == want, (a, c, m, k)
+
+
+def test_host_hash_matches_oracle_on_random_and_edge_operands(L):
+    """The library's divide-free remainders (fold mod p, Lemire mod m) against
+    the oracle's plain 64-bit `%`, over random and boundary operands."""
+    rng = random.Random(5)
+    ms = [1, 2, 3, 5, 7, 16, 72818, 1 << 20, 16946683, 2**31 - 1, 2**31, 2**31 + 1,
+          2**32 - 5, 2**32 - 2, 2**32 - 1] + [rng.randrange(1, 2**32) for _ in range(20)]
+    edge_k = [0, 1, 2, 3, 4, 5, 2**31 - 1, 2**31, 2**32 - 6, 2**32 - 5, 2**32 - 4, 2**32 - 2, 2**32 - 1]
+    keys = np.array(edge_k + [rng.randrange(0, 2**32) for _ in range(3000)], dtype=np.uint32)
+    consts = [(1, 0), (O.PRIME - 1, O.PRIME - 1), (2**32 - 1, 2**32 - 1), (2**31, 5)] + \
+             [(rng.randrange(1, O.PRIME), rng.randrange(0, O.PRIME)) for _ in range(6)]
+    for m in ms:
+        for a, c in consts:
+            got = _host_hash(L, a, c, m, keys)
+            want = [O.hash_value(a, c, m, int(k)) for k in keys[:400]]
+            assert got[:400].tolist() == want, (a, c, m)
+            # the rest in bulk with numpy's exact uint64 arithmetic on small products
+            if a < 2**16:
+                x = (np.uint64(a) * keys.astype(np.uint64) + np.uint64(c)) % np.uint64(O.PRIME) % np.uint64(m)
+                assert (got == x.astype(np.uint32)).all()
+
+
+def test_host_hash_rejects_zero_buckets(L):
+    with pytest.raises(L.GhtError):
+        L.ght_hash_host(1, 0, 0, np.zeros(1, np.uint32), np.zeros(1, np.uint32), 1)
