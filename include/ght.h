@@ -76,9 +76,23 @@ typedef struct {
   uint32_t max_chain;    /* cuckoo exchanges per insert before failing (default 1000) */
   uint32_t max_attempts; /* builds with fresh constants before GHT_ERR_BUILD_FAILED (default 50, Sec. VII) */
   int32_t count_probes;  /* 1: kernels accumulate probe counters (slower; off for timing) */
-  int32_t tile_lanes;    /* lanes that read one bucket together: 4, 8 or 16 (default 8) */
-  int32_t blocks_per_sm; /* grid = SMs x this; 0 = as many as fit */
-  int32_t reserved[8];
+  /* Launch shapes (0 = tuned default). Find: lanes that read one bucket
+   * together (4, 8 or 16; 8 or 16 for 32-pair buckets; 8 for schemes other
+   * than BCHT), queries each lane keeps in flight (1 or 2), blocks per SM.
+   * Build: the same three for the insert kernel. */
+  int32_t tile_lanes;
+  int32_t blocks_per_sm;
+  int32_t keys_per_lane;
+  int32_t build_tile_lanes;
+  int32_t build_keys_per_lane;
+  int32_t build_blocks_per_sm;
+  /* Grouped build (opt-in, 1): the pairs are first regrouped by first-choice
+   * bucket range (H_0(k) >> s) and inserted group after group, so concurrent
+   * inserts touch a small window of the table. Needs scratch
+   * (ght_build_scratch_bytes), else the build inserts in input order. 0 or
+   * -1: input order (default). */
+  int32_t group_build;
+  int32_t reserved[3];
 } ght_config;
 
 typedef struct {
@@ -96,11 +110,13 @@ typedef struct {
   uint64_t find_queries;       /* queries answered since the last reset */
   uint64_t table_bytes;        /* device bytes of the table (control block + slots) */
   int32_t built;
-  int32_t tile_lanes;
-  /* device time of the last successful build's fill and insert kernels and
+  int32_t tile_lanes, keys_per_lane, build_tile_lanes, build_keys_per_lane;
+  /* device time of the last build's fill, grouping and insert kernels and
    * of the last find kernel, from events on the table's stream (-1 if not
    * yet complete) */
-  double last_fill_ms, last_insert_ms, last_find_ms;
+  double last_fill_ms, last_insert_ms, last_find_ms, last_group_ms;
+  int32_t last_build_grouped;
+  int32_t pad0;
 } ght_stats_t;
 
 /* Library version string; never NULL. */
@@ -144,11 +160,22 @@ int ght_build(ght_table *t, const uint32_t *d_keys, const uint32_t *d_values, ui
  * successful build. */
 int ght_find(const ght_table *t, const uint32_t *d_queries, uint32_t *d_out, uint64_t n);
 
-/* As ght_build / ght_find with HOST arrays: the library copies through
- * pinned staging buffers in chunks, overlapping host<->device copies with
- * the kernels, and returns when the results are in h_out. */
+/* As ght_build / ght_find with HOST arrays: the library stages them in
+ * device memory from its own stream-ordered pool (find pipelines chunked
+ * host<->device copies with the kernel) and returns when the table is built
+ * or the results are in h_out. Pinned host memory copies fastest. */
 int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_values, uint64_t n);
 int ght_find_host(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out, uint64_t n);
+
+/* Device scratch a build of n keys uses for grouping (0 if this table
+ * builds without grouping). */
+uint64_t ght_build_scratch_bytes(const ght_table *t, uint64_t n);
+
+/* Caller-owned device scratch (256-byte aligned, `bytes` long, kept alive
+ * by the caller) for later builds; NULL clears it. Without it, a table whose
+ * storage the library owns takes grouping scratch from the library's
+ * stream-ordered pool, and a table on caller storage builds ungrouped. */
+int ght_set_build_scratch(ght_table *t, void *d_scratch, uint64_t bytes);
 
 /* Fill *out (synchronises the stream when probe counters are on). */
 int ght_stats(const ght_table *t, ght_stats_t *out);

@@ -31,7 +31,9 @@ class GhtConfig(C.Structure):
     _fields_ = [
         ("bucket_size", C.c_int32), ("num_hashes", C.c_int32), ("threshold", C.c_int32),
         ("max_chain", C.c_uint32), ("max_attempts", C.c_uint32), ("count_probes", C.c_int32),
-        ("tile_lanes", C.c_int32), ("blocks_per_sm", C.c_int32), ("reserved", C.c_int32 * 8),
+        ("tile_lanes", C.c_int32), ("blocks_per_sm", C.c_int32), ("keys_per_lane", C.c_int32),
+        ("build_tile_lanes", C.c_int32), ("build_keys_per_lane", C.c_int32),
+        ("build_blocks_per_sm", C.c_int32), ("group_build", C.c_int32), ("reserved", C.c_int32 * 3),
     ]
 
 
@@ -44,7 +46,9 @@ class GhtStats(C.Structure):
         ("hash_c", C.c_uint32 * 4), ("insert_probes", C.c_uint64), ("insert_retries", C.c_uint64),
         ("insert_evictions", C.c_uint64), ("longest_chain", C.c_uint64), ("find_probes", C.c_uint64), ("find_queries", C.c_uint64),
         ("table_bytes", C.c_uint64), ("built", C.c_int32), ("tile_lanes", C.c_int32),
+        ("keys_per_lane", C.c_int32), ("build_tile_lanes", C.c_int32), ("build_keys_per_lane", C.c_int32),
         ("last_fill_ms", C.c_double), ("last_insert_ms", C.c_double), ("last_find_ms", C.c_double),
+        ("last_group_ms", C.c_double), ("last_build_grouped", C.c_int32), ("pad0", C.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -88,6 +92,8 @@ def lib():
                 "ght_build_host": ([vp, vp, vp, u64], i32),
                 "ght_find_host": ([vp, vp, vp, u64], i32),
                 "ght_stats": ([vp, C.POINTER(GhtStats)], i32),
+                "ght_build_scratch_bytes": ([vp, u64], u64),
+                "ght_set_build_scratch": ([vp, vp, u64], i32),
                 "ght_reset_counters": ([vp], i32),
                 "ght_export": ([vp, vp, u64], i32),
                 "ght_hash_device": ([vp, vp, vp, u64], i32),
@@ -185,6 +191,14 @@ def ght_find_host(t: int, h_queries, h_out, n: int) -> None:
     _check(lib().ght_find_host(t, _ptr(h_queries), _ptr(h_out), n))
 
 
+def ght_build_scratch_bytes(t: int, n: int) -> int:
+    return int(lib().ght_build_scratch_bytes(t, n))
+
+
+def ght_set_build_scratch(t: int, d_scratch, nbytes: int) -> None:
+    _check(lib().ght_set_build_scratch(t, _ptr(d_scratch), nbytes))
+
+
 def ght_stats(t: int) -> GhtStats:
     s = GhtStats()
     _check(lib().ght_stats(t, C.byref(s)))
@@ -277,10 +291,29 @@ class HashTable:
             raise ValueError("keys and values differ in length")
         with _device_of(self.device):
             self._stream()
+            self._ensure_scratch(k.numel())
             if k.is_cuda:
                 ght_build(self._t, k, v, k.numel())
             else:
                 ght_build_host(self._t, k, v, k.numel())
+
+    def _ensure_scratch(self, n: int) -> None:
+        """Grouped builds need scratch; it is a torch tensor kept with the table."""
+        import torch
+        need = ght_build_scratch_bytes(self._t, n)
+        have = getattr(self, "_scratch_bytes", 0)
+        if need and need > have:
+            self._scratch = torch.empty(need + 256, dtype=torch.uint8, device=self.device)
+            base = self._scratch.data_ptr()
+            ght_set_build_scratch(self._t, (base + 255) & ~255, need)
+            self._scratch_bytes = need
+
+    def release_scratch(self) -> None:
+        """Drop the grouping scratch (later large builds run ungrouped until re-set)."""
+        if getattr(self, "_scratch_bytes", 0):
+            ght_set_build_scratch(self._t, None, 0)
+            self._scratch = None
+            self._scratch_bytes = 0
 
     def find(self, queries, out=None):
         import torch

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libght.so")
-SOURCES = ["ght_api.cu", "kern_bcht.cu", "kern_other.cu"]
+SOURCES = ["ght_api.cu", "kern_bcht.cu", "kern_other.cu", "kern_group.cu"]
 HEADERS = ["ght_device.cuh", "ght_kernels.cuh", "ght_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

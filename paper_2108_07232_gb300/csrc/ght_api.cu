@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <thread>
 
@@ -71,7 +72,10 @@ constexpr uint64_t kCtrlBytes = sizeof(ght::Ctrl);
 struct Shape {
   int scheme, b, h, t;
   uint32_t max_chain, max_attempts;
-  int count_probes, tile_lanes, blocks_per_sm;
+  int count_probes;
+  int tile_lanes, blocks_per_sm, keys_per_lane;                    // find
+  int build_tile_lanes, build_blocks_per_sm, build_keys_per_lane;  // build
+  int group_build;  // 1: group the input by first-choice bucket range before inserting
   uint64_t m;
 };
 
@@ -86,7 +90,13 @@ int default_config(int scheme, ght_config *c) {
     default: return fail(GHT_ERR_INVALID_ARG, "unknown scheme %d", scheme);
   }
   c->max_attempts = 50;
-  c->tile_lanes = scheme == GHT_CUCKOO1 ? 1 : 8;
+  // tile shapes: measured defaults for 16-pair BCHT buckets on GB300; 8 lanes
+  // elsewhere (the only shape instantiated for the other schemes)
+  const bool bcht16 = scheme == GHT_BCHT;
+  c->tile_lanes = scheme == GHT_CUCKOO1 ? 1 : (bcht16 ? 4 : 8);
+  c->keys_per_lane = 2;
+  c->build_tile_lanes = scheme == GHT_CUCKOO1 ? 1 : (bcht16 ? 16 : 8);
+  c->build_keys_per_lane = bcht16 ? 1 : 2;
   return GHT_OK;
 }
 
@@ -100,9 +110,15 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
     if (user->num_hashes) d.num_hashes = user->num_hashes;
     if (user->max_chain) d.max_chain = user->max_chain;
     if (user->max_attempts) d.max_attempts = user->max_attempts;
+    if (user->bucket_size == 32 && scheme == GHT_BCHT) d.tile_lanes = d.build_tile_lanes = 8;
     if (user->tile_lanes) d.tile_lanes = user->tile_lanes;
+    if (user->build_tile_lanes) d.build_tile_lanes = user->build_tile_lanes;
     d.count_probes = user->count_probes;
     d.blocks_per_sm = user->blocks_per_sm;
+    d.build_blocks_per_sm = user->build_blocks_per_sm;
+    if (user->keys_per_lane) d.keys_per_lane = user->keys_per_lane;
+    if (user->build_keys_per_lane) d.build_keys_per_lane = user->build_keys_per_lane;
+    d.group_build = user->group_build;
     if (user->threshold) d.threshold = user->threshold;
     else if (scheme == GHT_IHT) d.threshold = (4 * d.bucket_size + 4) / 5;  // ceil(0.8 b)
   }
@@ -117,10 +133,13 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
     if (scheme == GHT_IHT && h != 3) return fail(GHT_ERR_INVALID_ARG, "IHT uses 3 hash functions");
     if ((scheme == GHT_BCHT || scheme == GHT_BCHT_LB) && (h < 2 || h > 4))
       return fail(GHT_ERR_INVALID_ARG, "BCHT needs 2..4 hash functions");
-    const bool ok = scheme == GHT_BCHT ? ght::bcht_shape_supported(b, d.tile_lanes)
-                                       : ght::other_shape_supported(scheme, b, d.tile_lanes);
-    if (!ok) return fail(GHT_ERR_INVALID_ARG, "tile of %d lanes unsupported for bucket size %d", d.tile_lanes, b);
+    for (int g : {d.tile_lanes, d.build_tile_lanes}) {
+      const bool ok = scheme == GHT_BCHT ? ght::bcht_shape_supported(b, g) : ght::other_shape_supported(scheme, b, g);
+      if (!ok) return fail(GHT_ERR_INVALID_ARG, "tile of %d lanes unsupported for bucket size %d", g, b);
+    }
   }
+  if ((d.keys_per_lane != 1 && d.keys_per_lane != 2) || (d.build_keys_per_lane != 1 && d.build_keys_per_lane != 2))
+    return fail(GHT_ERR_INVALID_ARG, "keys per lane must be 1 or 2");
   if (scheme == GHT_IHT && (d.threshold < 1 || d.threshold > b + 1))
     return fail(GHT_ERR_INVALID_ARG, "IHT threshold %d outside [1, b+1]", d.threshold);
   // Sec. III: C = m b, load factor n / C  =>  m = ceil(capacity / (lf b))
@@ -136,6 +155,11 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
   s->count_probes = d.count_probes;
   s->tile_lanes = d.tile_lanes;
   s->blocks_per_sm = d.blocks_per_sm;
+  s->keys_per_lane = d.keys_per_lane;
+  s->build_tile_lanes = d.build_tile_lanes;
+  s->build_blocks_per_sm = d.build_blocks_per_sm;
+  s->build_keys_per_lane = d.build_keys_per_lane;
+  s->group_build = d.group_build;
   s->m = (uint64_t)want;
   return GHT_OK;
 }
@@ -143,6 +167,54 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
 uint64_t bytes_of(const Shape &s) {
   const uint64_t slots = s.m * (uint64_t)s.b * 8ull;
   return kCtrlBytes + ((slots + 255ull) & ~255ull);
+}
+
+// The library's own stream-ordered pool (one per device) for staging and
+// grouping scratch of tables whose storage the library owns. Freed blocks
+// stay cached in the pool, so repeated builds do not return to the driver.
+cudaError_t library_pool(cudaMemPool_t *out) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    e = cudaMemPoolCreate(&pools[dev], &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  *out = pools[dev];
+  return cudaSuccess;
+}
+
+cudaError_t pool_alloc(void **p, uint64_t bytes, cudaStream_t s) {
+  cudaMemPool_t pool;
+  const cudaError_t e = library_pool(&pool);
+  if (e != cudaSuccess) return e;
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+// Grouping shape: at most 512 groups of 2^shift consecutive buckets.
+void group_shape(uint64_t m, int *shift, uint32_t *groups) {
+  int bits = 0;
+  while ((1ull << bits) < m) ++bits;
+  *shift = bits > 9 ? bits - 9 : 0;
+  *groups = (uint32_t)(((m - 1) >> *shift) + 1);
+}
+
+// Scratch of a grouped build: counts and cursors, then the regrouped keys and values.
+uint64_t group_scratch_bytes(uint64_t n) {
+  const uint64_t head = 2ull * ght::kMaxGroups * sizeof(uint32_t);
+  const uint64_t arr = (n * sizeof(uint32_t) + 255ull) & ~255ull;
+  return head + 2 * arr;
 }
 
 }  // namespace
@@ -165,8 +237,12 @@ struct ght_table {
   uint32_t attempts = 0;
   ght::Ctrl *h_ctrl = nullptr;  // pinned mirror of the control block
   cudaEvent_t done = nullptr;
-  cudaEvent_t tev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // fill, fill end, insert end, find, find end
+  // timing events: fill start, fill end, grouping end, insert end, find start, find end
+  cudaEvent_t tev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   bool timed_build = false;
+  bool last_grouped = false;
+  void *scratch = nullptr;  // caller-owned grouping scratch (ght_set_build_scratch)
+  uint64_t scratch_bytes = 0;
   mutable bool timed_find = false;
   mutable uint64_t insert_probes = 0, insert_retries = 0, insert_evictions = 0, longest_chain = 0;
 
@@ -204,10 +280,20 @@ struct ght_table {
     return v;
   }
 
-  ght::LaunchOpts opts() const {
+  ght::LaunchOpts find_opts() const {
     ght::LaunchOpts o;
     o.tile_lanes = shape.tile_lanes;
     o.blocks_per_sm = shape.blocks_per_sm;
+    o.keys_per_lane = shape.keys_per_lane;
+    o.count = shape.count_probes != 0;
+    return o;
+  }
+
+  ght::LaunchOpts build_opts() const {
+    ght::LaunchOpts o;
+    o.tile_lanes = shape.build_tile_lanes;
+    o.blocks_per_sm = shape.build_blocks_per_sm;
+    o.keys_per_lane = shape.build_keys_per_lane;
     o.count = shape.count_probes != 0;
     return o;
   }
@@ -215,16 +301,28 @@ struct ght_table {
 
 namespace {
 
-cudaError_t launch_insert(const ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n) {
+cudaError_t launch_insert(const ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n,
+                          bool dynamic = false) {
   const ght::TableView tv = t->view();
-  if (t->shape.scheme == GHT_BCHT) return ght::launch_insert_bcht(t->shape.b, tv, k, v, n, t->opts(), t->stream);
-  return ght::launch_insert_other(t->shape.scheme, t->shape.b, tv, k, v, n, t->opts(), t->stream);
+  ght::LaunchOpts o = t->build_opts();
+  o.dynamic = dynamic;
+  if (t->shape.scheme == GHT_BCHT) return ght::launch_insert_bcht(t->shape.b, tv, k, v, n, o, t->stream);
+  return ght::launch_insert_other(t->shape.scheme, t->shape.b, tv, k, v, n, o, t->stream);
+}
+
+// Whether a build of n keys groups its input first (opt-in: on GB300 the
+// grouping pass costs more than the locality saves, see the design notes);
+// it also needs scratch (caller-set, or the library pool when the library
+// owns the table storage).
+bool wants_grouping(const ght_table *t, uint64_t n) {
+  if (t->shape.scheme == GHT_CUCKOO1 || n == 0 || n > 0xFFFFFFFFull) return false;
+  return t->shape.group_build > 0;
 }
 
 cudaError_t launch_find(const ght_table *t, const uint32_t *q, uint32_t *out, uint64_t n) {
   const ght::TableView tv = t->view();
-  if (t->shape.scheme == GHT_BCHT) return ght::launch_find_bcht(t->shape.b, tv, q, out, n, t->opts(), t->stream);
-  return ght::launch_find_other(t->shape.scheme, t->shape.b, tv, q, out, n, t->opts(), t->stream);
+  if (t->shape.scheme == GHT_BCHT) return ght::launch_find_bcht(t->shape.b, tv, q, out, n, t->find_opts(), t->stream);
+  return ght::launch_find_other(t->shape.scheme, t->shape.b, tv, q, out, n, t->find_opts(), t->stream);
 }
 
 // Read the control block after the stream's work; bounded wait.
@@ -236,26 +334,55 @@ int read_ctrl(const ght_table *t) {
   return wait_event(t->done, wait_limit_seconds());
 }
 
-// One build from device-resident keys: fill, insert, status; retry with the
-// next attempt's constants on failure.
+// One build from device-resident keys: fill, (group,) insert, status; retry
+// with the next attempt's constants on failure.
 int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n, uint32_t first_attempt) {
   t->built = false;
   t->n_stored = 0;
+  bool grouped = wants_grouping(t, n);
+  void *pool_buf = nullptr;
+  char *scr = nullptr;
+  if (grouped) {
+    const uint64_t need = group_scratch_bytes(n);
+    if (t->scratch && t->scratch_bytes >= need) {
+      scr = static_cast<char *>(t->scratch);
+    } else if (t->owns_storage && pool_alloc(&pool_buf, need, t->stream) == cudaSuccess) {
+      scr = static_cast<char *>(pool_buf);
+    } else {
+      cudaGetLastError();
+      grouped = false;  // no scratch: build in input order
+    }
+  }
+  int shift = 0;
+  uint32_t groups = 1;
+  group_shape(t->shape.m, &shift, &groups);
+  uint32_t *counts = reinterpret_cast<uint32_t *>(scr);
+  uint32_t *cursors = counts + ght::kMaxGroups;
+  uint32_t *gk = reinterpret_cast<uint32_t *>(scr + 2ull * ght::kMaxGroups * sizeof(uint32_t));
+  uint32_t *gv = gk + (((n * sizeof(uint32_t) + 255ull) & ~255ull) / sizeof(uint32_t));
+  int rc = fail(GHT_ERR_BUILD_FAILED, "build failed in %u attempts (chain bound or full buckets)",
+                t->shape.max_attempts);
   for (uint32_t attempt = first_attempt; attempt < t->shape.max_attempts; ++attempt) {
     t->derive(attempt);
     const ght::TableView tv = t->view();
     cudaEventRecord(t->tev[0], t->stream);
     cudaError_t e = ght::launch_fill(tv, t->shape.m * (uint64_t)t->shape.b, t->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "launching fill");
+    if (e != cudaSuccess) { rc = cuda_fail(e, "launching fill"); break; }
     cudaEventRecord(t->tev[1], t->stream);
-    if (n > 0) {
-      e = launch_insert(t, k, v, n);
-      if (e != cudaSuccess) return cuda_fail(e, "launching insert");
+    if (grouped) {
+      e = ght::launch_group(tv, k, v, n, shift, groups, counts, cursors, gk, gv, t->stream);
+      if (e != cudaSuccess) { rc = cuda_fail(e, "launching grouping"); break; }
     }
     cudaEventRecord(t->tev[2], t->stream);
+    if (n > 0) {
+      e = grouped ? launch_insert(t, gk, gv, n, true) : launch_insert(t, k, v, n);
+      if (e != cudaSuccess) { rc = cuda_fail(e, "launching insert"); break; }
+    }
+    cudaEventRecord(t->tev[3], t->stream);
     t->timed_build = true;
-    int rc = read_ctrl(t);
-    if (rc) return rc;
+    t->last_grouped = grouped;
+    rc = read_ctrl(t);
+    if (rc) break;
     const uint32_t st = t->h_ctrl->status;
     t->attempts = attempt + 1;
     t->insert_probes = t->h_ctrl->insert_probes;
@@ -265,13 +392,16 @@ int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n,
     if (st == 0u) {
       t->built = true;
       t->n_stored = n;
-      return GHT_OK;
+      rc = GHT_OK;
+      break;
     }
-    if (st & ght::kStatusSentinel) return fail(GHT_ERR_SENTINEL_KEY, "an input key is the sentinel 0xFFFFFFFF");
-    if (st & ght::kStatusTimeout) return fail(GHT_ERR_DEVICE_TIMEOUT, "a key exceeded the per-key step bound");
-    if (st & ght::kStatusCorrupt) return fail(GHT_ERR_CUDA, "table corrupt: an evicted key did not hash to its bucket");
+    if (st & ght::kStatusSentinel) { rc = fail(GHT_ERR_SENTINEL_KEY, "an input key is the sentinel 0xFFFFFFFF"); break; }
+    if (st & ght::kStatusTimeout) { rc = fail(GHT_ERR_DEVICE_TIMEOUT, "a key exceeded the per-key step bound"); break; }
+    if (st & ght::kStatusCorrupt) { rc = fail(GHT_ERR_CUDA, "table corrupt: an evicted key did not hash to its bucket"); break; }
+    rc = fail(GHT_ERR_BUILD_FAILED, "build failed in %u attempts (chain bound or full buckets)", t->shape.max_attempts);
   }
-  return fail(GHT_ERR_BUILD_FAILED, "build failed in %u attempts (chain bound or full buckets)", t->shape.max_attempts);
+  if (pool_buf) cudaFreeAsync(pool_buf, t->stream);
+  return rc;
 }
 
 constexpr uint64_t kChunk = 1ull << 23;  // keys per host<->device pipeline chunk
@@ -337,7 +467,7 @@ ght_table *ght_create_ex(int scheme, uint64_t capacity, double load_factor, uint
   t->slots = reinterpret_cast<uint64_t *>(reinterpret_cast<char *>(t->storage) + kCtrlBytes);
   cudaError_t e = cudaMallocHost(reinterpret_cast<void **>(&t->h_ctrl), kCtrlBytes);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->done, cudaEventDisableTiming);
-  for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaEventCreate(&t->tev[i]);
+  for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreate(&t->tev[i]);
   if (e != cudaSuccess) {
     cuda_fail(e, "creating table resources");
     ght_destroy(t);
@@ -371,10 +501,10 @@ int ght_find(const ght_table *t, const uint32_t *d_queries, uint32_t *d_out, uin
   if (!t->built) return fail(GHT_ERR_NOT_BUILT, "table has no successful build");
   if (n == 0) return GHT_OK;
   if (!d_queries || !d_out) return fail(GHT_ERR_INVALID_ARG, "queries or out is NULL");
-  cudaEventRecord(t->tev[3], t->stream);
+  cudaEventRecord(t->tev[4], t->stream);
   const cudaError_t e = launch_find(t, d_queries, d_out, n);
   if (e != cudaSuccess) return cuda_fail(e, "launching find");
-  cudaEventRecord(t->tev[4], t->stream);
+  cudaEventRecord(t->tev[5], t->stream);
   t->timed_find = true;
   return GHT_OK;
 }
@@ -385,74 +515,26 @@ int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_value
                                    (unsigned long long)t->capacity);
   if (n > 0 && (!h_keys || !h_values)) return fail(GHT_ERR_INVALID_ARG, "keys or values is NULL");
   if (n == 0) return build_device(t, nullptr, nullptr, 0, 0);
-  // Stage the pairs on the device chunk by chunk on a copy stream while the
-  // first attempt inserts each chunk as soon as it has landed; later
-  // attempts (rare) rebuild from the staged copy.
-  uint32_t *d_buf = nullptr;
-  cudaStream_t copy = nullptr;
-  cudaEvent_t landed[2] = {nullptr, nullptr};
+  // Stage the pairs on the device (two copies on the table stream; the
+  // library pool keeps the staging block for the next call), then build.
+  void *buf = nullptr;
+  const uint64_t arr = (n * sizeof(uint32_t) + 255ull) & ~255ull;
+  cudaError_t e = pool_alloc(&buf, 2 * arr, t->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GHT_ERR_OOM, "staging allocation: %s", cudaGetErrorString(e));
+  }
+  uint32_t *d_k = static_cast<uint32_t *>(buf), *d_v = d_k + arr / sizeof(uint32_t);
   int rc = GHT_OK;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&d_buf), 2 * n * sizeof(uint32_t), t->stream);
-  if (e != cudaSuccess) return fail(GHT_ERR_OOM, "staging allocation: %s", cudaGetErrorString(e));
-  uint32_t *d_k = d_buf, *d_v = d_buf + n;
-  if ((e = cudaStreamCreateWithFlags(&copy, cudaStreamNonBlocking)) != cudaSuccess ||
-      (e = cudaEventCreateWithFlags(&landed[0], cudaEventDisableTiming)) != cudaSuccess ||
-      (e = cudaEventCreateWithFlags(&landed[1], cudaEventDisableTiming)) != cudaSuccess) {
-    rc = cuda_fail(e, "creating pipeline resources");
-  }
-  if (rc == GHT_OK) {
-    // the staging buffer is ready once the table stream has allocated it
-    if ((e = cudaEventRecord(landed[0], t->stream)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(copy, landed[0], 0)) != cudaSuccess)
-      rc = cuda_fail(e, "ordering the staging copy");
-  }
-  if (rc == GHT_OK) {
-    t->built = false;
-    t->derive(0);
-    const ght::TableView tv = t->view();
-    if ((e = ght::launch_fill(tv, t->shape.m * (uint64_t)t->shape.b, t->stream)) != cudaSuccess)
-      rc = cuda_fail(e, "launching fill");
-    for (uint64_t off = 0, i = 0; rc == GHT_OK && off < n; off += kChunk, ++i) {
-      const uint64_t len = std::min(kChunk, n - off);
-      cudaEvent_t ev = landed[i & 1];
-      if ((e = cudaMemcpyAsync(d_k + off, h_keys + off, len * 4, cudaMemcpyHostToDevice, copy)) != cudaSuccess ||
-          (e = cudaMemcpyAsync(d_v + off, h_values + off, len * 4, cudaMemcpyHostToDevice, copy)) != cudaSuccess ||
-          (e = cudaEventRecord(ev, copy)) != cudaSuccess || (e = cudaStreamWaitEvent(t->stream, ev, 0)) != cudaSuccess) {
-        rc = cuda_fail(e, "staging keys");
-        break;
-      }
-      if ((e = launch_insert(t, d_k + off, d_v + off, len)) != cudaSuccess) rc = cuda_fail(e, "launching insert");
-    }
-    if (rc == GHT_OK) rc = read_ctrl(t);
-    if (rc == GHT_OK) {
-      const uint32_t st = t->h_ctrl->status;
-      t->attempts = 1;
-      t->insert_probes = t->h_ctrl->insert_probes;
-      t->insert_retries = t->h_ctrl->insert_retries;
-      t->insert_evictions = t->h_ctrl->insert_evictions;
-      t->longest_chain = t->h_ctrl->longest_chain;
-      if (st == 0u) {
-        t->built = true;
-        t->n_stored = n;
-      } else if (st & ght::kStatusSentinel) {
-        rc = fail(GHT_ERR_SENTINEL_KEY, "an input key is the sentinel 0xFFFFFFFF");
-      } else if (st & ght::kStatusTimeout) {
-        rc = fail(GHT_ERR_DEVICE_TIMEOUT, "a key exceeded the per-key step bound");
-      } else if (st & ght::kStatusCorrupt) {
-        rc = fail(GHT_ERR_CUDA, "table corrupt: an evicted key did not hash to its bucket");
-      } else {
-        rc = build_device(t, d_k, d_v, n, 1);
-      }
-    }
-  }
-  cudaFreeAsync(d_buf, t->stream);
+  if ((e = cudaMemcpyAsync(d_k, h_keys, n * 4, cudaMemcpyHostToDevice, t->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_v, h_values, n * 4, cudaMemcpyHostToDevice, t->stream)) != cudaSuccess)
+    rc = cuda_fail(e, "staging keys");
+  if (rc == GHT_OK) rc = build_device(t, d_k, d_v, n, 0);
+  cudaFreeAsync(buf, t->stream);
   if (rc == GHT_OK) {
     e = cudaEventRecord(t->done, t->stream);
     rc = e == cudaSuccess ? wait_event(t->done, wait_limit_seconds()) : cuda_fail(e, "recording an event");
   }
-  if (landed[0]) cudaEventDestroy(landed[0]);
-  if (landed[1]) cudaEventDestroy(landed[1]);
-  if (copy) cudaStreamDestroy(copy);
   return rc;
 }
 
@@ -468,8 +550,11 @@ int ght_find_host(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out
   const uint64_t nchunks = (n + kChunk - 1) / kChunk;
   cudaEvent_t evs[8] = {};
   int rc = GHT_OK;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&d_buf), 2 * n * sizeof(uint32_t), t->stream);
-  if (e != cudaSuccess) return fail(GHT_ERR_OOM, "staging allocation: %s", cudaGetErrorString(e));
+  cudaError_t e = pool_alloc(reinterpret_cast<void **>(&d_buf), 2 * n * sizeof(uint32_t), t->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GHT_ERR_OOM, "staging allocation: %s", cudaGetErrorString(e));
+  }
   uint32_t *d_q = d_buf, *d_o = d_buf + n;
   if ((e = cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking)) != cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking)) != cudaSuccess)
@@ -520,6 +605,22 @@ int ght_find_host(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out
   return rc;
 }
 
+uint64_t ght_build_scratch_bytes(const ght_table *t, uint64_t n) {
+  if (!t) {
+    fail(GHT_ERR_INVALID_ARG, "table is NULL");
+    return 0;
+  }
+  return wants_grouping(t, n) ? group_scratch_bytes(n) : 0;
+}
+
+int ght_set_build_scratch(ght_table *t, void *d_scratch, uint64_t bytes) {
+  if (!t) return fail(GHT_ERR_INVALID_ARG, "table is NULL");
+  if (d_scratch && ((uintptr_t)d_scratch & 255u) != 0u) return fail(GHT_ERR_INVALID_ARG, "scratch must be 256-byte aligned");
+  t->scratch = d_scratch;
+  t->scratch_bytes = d_scratch ? bytes : 0;
+  return GHT_OK;
+}
+
 int ght_stats(const ght_table *t, ght_stats_t *out) {
   if (!t || !out) return fail(GHT_ERR_INVALID_ARG, "table or out is NULL");
   memset(out, 0, sizeof *out);
@@ -541,18 +642,24 @@ int ght_stats(const ght_table *t, ght_stats_t *out) {
   out->table_bytes = t->storage_bytes;
   out->built = t->built ? 1 : 0;
   out->tile_lanes = t->shape.tile_lanes;
+  out->keys_per_lane = t->shape.keys_per_lane;
+  out->build_tile_lanes = t->shape.build_tile_lanes;
+  out->build_keys_per_lane = t->shape.build_keys_per_lane;
   out->insert_probes = t->insert_probes;
   out->insert_retries = t->insert_retries;
   out->insert_evictions = t->insert_evictions;
   out->longest_chain = t->longest_chain;
   out->last_fill_ms = out->last_insert_ms = out->last_find_ms = -1.0;
   float ms = 0.f;
-  if (t->timed_build && cudaEventQuery(t->tev[2]) == cudaSuccess) {
+  out->last_group_ms = -1.0;
+  out->last_build_grouped = t->last_grouped ? 1 : 0;
+  if (t->timed_build && cudaEventQuery(t->tev[3]) == cudaSuccess) {
     if (cudaEventElapsedTime(&ms, t->tev[0], t->tev[1]) == cudaSuccess) out->last_fill_ms = ms;
-    if (cudaEventElapsedTime(&ms, t->tev[1], t->tev[2]) == cudaSuccess) out->last_insert_ms = ms;
+    if (cudaEventElapsedTime(&ms, t->tev[1], t->tev[2]) == cudaSuccess) out->last_group_ms = ms;
+    if (cudaEventElapsedTime(&ms, t->tev[2], t->tev[3]) == cudaSuccess) out->last_insert_ms = ms;
   }
-  if (t->timed_find && cudaEventQuery(t->tev[4]) == cudaSuccess &&
-      cudaEventElapsedTime(&ms, t->tev[3], t->tev[4]) == cudaSuccess)
+  if (t->timed_find && cudaEventQuery(t->tev[5]) == cudaSuccess &&
+      cudaEventElapsedTime(&ms, t->tev[4], t->tev[5]) == cudaSuccess)
     out->last_find_ms = ms;
   cudaGetLastError();
   if (t->shape.count_probes) {

@@ -32,7 +32,8 @@ struct Ctrl {
   unsigned long long find_probes;
   unsigned long long find_queries;
   unsigned long long longest_chain;
-  unsigned long long reserved[25];
+  unsigned long long work_cursor;  // next input index claimed by a dynamic-chunk build
+  unsigned long long reserved[24];
 };
 static_assert(sizeof(Ctrl) == 256, "control block is 256 bytes");
 

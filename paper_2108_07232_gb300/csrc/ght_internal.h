@@ -11,11 +11,17 @@
 
 namespace ght {
 
+// Launch shape of one kernel: lanes per bucket tile, keys each lane keeps
+// in flight, and the grid (0 = as many blocks as are resident at once).
 struct LaunchOpts {
-  int tile_lanes = 8;     // lanes per bucket tile
-  int blocks_per_sm = 0;  // 0 = occupancy limit
-  bool count = false;     // probe counters
+  int tile_lanes = 8;
+  int keys_per_lane = 2;
+  int blocks_per_sm = 0;
+  bool count = false;    // probe counters
+  bool dynamic = false;  // build: warps claim 32-pair chunks from a global cursor
 };
+
+constexpr uint32_t kMaxGroups = 4096;
 
 constexpr int kThreads = 256;
 
@@ -73,5 +79,10 @@ bool other_shape_supported(int scheme, int B, int G);
 cudaError_t launch_fill(const TableView &tv, uint64_t num_slots, cudaStream_t s);
 cudaError_t launch_hash(const TableView &tv, const uint32_t *k, uint32_t *out, uint64_t n,
                         cudaStream_t s);
+
+// kern_group.cu: reorder (keys, values) by H_0(k) >> shift into out_k/out_v.
+cudaError_t launch_group(const TableView &tv, const uint32_t *keys, const uint32_t *values, uint64_t n,
+                         int shift, uint32_t groups, uint32_t *counts, uint32_t *cursors, uint32_t *out_k,
+                         uint32_t *out_v, cudaStream_t s);
 
 }  // namespace ght

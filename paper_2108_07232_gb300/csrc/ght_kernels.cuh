@@ -23,97 +23,169 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 
 // ----------------------------------------------------------------------------
+// Input stream of a warp's slice, read 32 items at a time with one coalesced
+// load and kept two chunks ahead of use, so refilling a lane never waits on
+// memory. Chunk x lives in register x of lane i (entry i).
+struct StreamQueue {
+  uint64_t base;  // slice index of entry 0 of chunk a (warp-uniform)
+  int head;       // next unused entry of chunk a (warp-uniform)
+  uint32_t a, b, c;
+};
+
+__device__ __forceinline__ uint32_t stream_load(const uint32_t *__restrict__ p, uint64_t i, uint64_t end) {
+  return i < end ? __ldg(p + i) : kEmptyKey;
+}
+
+__device__ __forceinline__ void stream_init(StreamQueue &q, const uint32_t *__restrict__ p, uint64_t beg,
+                                            uint64_t end, int lane) {
+  q.base = beg;
+  q.head = 0;
+  q.a = stream_load(p, beg + lane, end);
+  q.b = stream_load(p, beg + 32 + lane, end);
+  q.c = stream_load(p, beg + 64 + lane, end);
+}
+
+// Hand the next popc(need) entries to the lanes set in `need` (in lane
+// order); returns the entry's slice index (>= end when the slice is spent).
+__device__ __forceinline__ uint64_t stream_take(StreamQueue &q, const uint32_t *__restrict__ p, uint64_t end,
+                                                unsigned need, unsigned below, int lane, uint32_t &item) {
+  const int pos = q.head + __popc(need & below);
+  const uint32_t from_a = __shfl_sync(kFull, q.a, pos & 31);
+  const uint32_t from_b = __shfl_sync(kFull, q.b, pos & 31);
+  item = pos < 32 ? from_a : from_b;
+  const uint64_t at = q.base + (uint64_t)pos;
+  q.head += __popc(need);
+  if (q.head >= 32) {
+    q.head -= 32;
+    q.base += 32;
+    q.a = q.b;
+    q.b = q.c;
+    q.c = stream_load(p, q.base + 64 + lane, end);
+  }
+  return ((need >> lane) & 1u) ? at : ~0ull;
+}
+
+// ----------------------------------------------------------------------------
 // Bucketed find. BCHT stops at the first probed bucket with an empty slot
 // (Sec. V-B find; valid because keys are placed in hash order and buckets
 // never lose keys). P2BHT, IHT and the load-balanced BCHT read their
 // candidates in order until the key is found (Sec. V-C, V-D find).
-template <int SCHEME, int B, int G, bool COUNT>
+//
+// Each lane owns KPL queries (sets). With KPL = 2 the sets are staggered:
+// one set's bucket reads are in flight while the other set is evaluated.
+// Tile members report a hit (and its value) or an empty slot to the owner
+// through per-warp shared memory rather than one ballot per slot.
+template <int SCHEME, int B, int G, int KPL, bool COUNT>
 __global__ void __launch_bounds__(256)
 bucketed_find_kernel(TableView tv, const uint32_t *__restrict__ queries, uint32_t *__restrict__ out,
                      uint64_t n, uint64_t per_warp) {
   constexpr int PPL = B / G;
   constexpr bool kEarlyExit = (SCHEME == kBCHT);
-  static_assert(B % G == 0 && 32 % G == 0 && PPL >= 1, "tile shape");
+  static_assert(B % G == 0 && 32 % G == 0 && PPL >= 1 && (KPL == 1 || KPL == 2), "tile shape");
+  __shared__ uint32_t s_hit[8][32], s_emp[8][32], s_val[8][32];
   const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
   const int r = lane & (G - 1);
   const int tbase = lane - r;
-  const unsigned tmask = (G == 32 ? kFull : ((1u << G) - 1u)) << tbase;
   const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t beg = warp * per_warp;
   if (beg >= n) return;  // whole warp
   const uint64_t end = beg + per_warp < n ? beg + per_warp : n;
   const unsigned below = lanemask_lt();
 
-  uint64_t cursor = beg, idx = 0;
-  bool active = false;
-  uint32_t key = 0, result = kEmptyKey;
-  int probe = 0;
+  StreamQueue sq;
+  stream_init(sq, queries, beg, end, lane);
+  bool active[KPL];
+  uint32_t key[KPL], act[KPL];
+  uint64_t idx[KPL];
+  int probe[KPL];
+  uint64_t v[KPL][G][PPL];
+#pragma unroll
+  for (int s = 0; s < KPL; ++s) {
+    active[s] = false;
+    key[s] = kEmptyKey;
+    act[s] = 0u;
+    idx[s] = 0;
+    probe[s] = 0;
+  }
   unsigned long long probes = 0, answered = 0;
 
   for (;;) {
-    const unsigned need = __ballot_sync(kFull, !active);
-    if (need != 0u && cursor < end) {
-      const uint64_t mine = cursor + __popc(need & below);
-      if (!active && mine < end) {
-        idx = mine;
-        key = __ldg(queries + mine);
-        result = kEmptyKey;
-        probe = 0;
-        if (COUNT) answered++;
-        if (key == kEmptyKey) out[idx] = kEmptyKey;  // the sentinel is never a key
-        else active = true;
-      }
-      cursor += __popc(need);
-      if (cursor > end) cursor = end;
-    }
-    const unsigned act = __ballot_sync(kFull, active);
-    if (act == 0u) {
-      if (cursor >= end) break;
-      continue;
-    }
-
-    const uint32_t myb = active ? bucket_of(tv.hf, probe, key) : 0u;
-    uint64_t v[G][PPL];
 #pragma unroll
-    for (int j = 0; j < G; ++j) {
-      const uint32_t bj = __shfl_sync(kFull, myb, tbase + j);
-      if ((act >> (tbase + j)) & 1u) load_part_ro<PPL>(tv.slots + (uint64_t)bj * B, r, v[j]);
-    }
-    bool finish = false;
-#pragma unroll
-    for (int j = 0; j < G; ++j) {
-      const uint32_t kj = __shfl_sync(kFull, key, tbase + j);
-      const bool aj = (act >> (tbase + j)) & 1u;
-      bool hit = false, emp = false;
-      uint32_t val = kEmptyKey;
-#pragma unroll
-      for (int p = 0; p < PPL; ++p) {
-        const uint32_t sk = pair_key(v[j][p]);
-        if (aj && !hit && sk == kj) {
-          hit = true;
-          val = pair_value(v[j][p]);
-        }
-        if (aj && sk == kEmptyKey) emp = true;
-      }
-      const unsigned hm = __ballot_sync(kFull, hit) & tmask;
-      const unsigned em = kEarlyExit ? (__ballot_sync(kFull, emp) & tmask) : 0u;
-      const uint32_t fv = __shfl_sync(kFull, val, hm ? (__ffs(hm) - 1) : lane);
-      if (lane == tbase + j && aj) {
-        if (COUNT) probes++;
-        if (hm) {
-          result = fv;
-          finish = true;
-        } else if (kEarlyExit && em) {
-          finish = true;
-        } else if (++probe >= tv.h) {
-          finish = true;
+    for (int s = 0; s < KPL; ++s) {
+      // refill set s from the stream, then issue its bucket reads
+      const unsigned need = __ballot_sync(kFull, !active[s]);
+      if (need != 0u && sq.base + sq.head < end) {
+        uint32_t k;
+        const uint64_t at = stream_take(sq, queries, end, need, below, lane, k);
+        if (at < end) {
+          if (COUNT) answered++;
+          if (k == kEmptyKey) {
+            out[at] = kEmptyKey;  // the sentinel is never a key
+          } else {
+            active[s] = true;
+            key[s] = k;
+            idx[s] = at;
+            probe[s] = 0;
+          }
         }
       }
+      act[s] = __ballot_sync(kFull, active[s]);
+      if (act[s] != 0u) {
+        const uint32_t myb = active[s] ? bucket_of(tv.hf, probe[s], key[s]) : 0u;
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+          const uint32_t bj = __shfl_sync(kFull, myb, tbase + j);
+          if ((act[s] >> (tbase + j)) & 1u) load_part_ro<PPL>(tv.slots + (uint64_t)bj * B, r, v[s][j]);
+        }
+      }
+      // evaluate the other set (or this one when KPL = 1)
+      const int e = (KPL == 1) ? s : (s + 1) % KPL;
+      if (act[e] != 0u) {
+        s_hit[wib][lane] = 0u;
+        if (kEarlyExit) s_emp[wib][lane] = 0u;
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+          const int owner = tbase + j;
+          const uint32_t kj = __shfl_sync(kFull, key[e], owner);
+          if ((act[e] >> owner) & 1u) {
+#pragma unroll
+            for (int p = 0; p < PPL; ++p) {
+              const uint32_t sk = pair_key(v[e][j][p]);
+              if (sk == kj) {
+                s_hit[wib][owner] = 1u;
+                s_val[wib][owner] = pair_value(v[e][j][p]);
+              }
+              if (kEarlyExit && sk == kEmptyKey) s_emp[wib][owner] = 1u;
+            }
+          }
+        }
+        __syncwarp();
+        if ((act[e] >> lane) & 1u) {
+          if (COUNT) probes++;
+          bool finish = false;
+          uint32_t result = kEmptyKey;
+          if (s_hit[wib][lane]) {
+            result = s_val[wib][lane];
+            finish = true;
+          } else if (kEarlyExit && s_emp[wib][lane]) {
+            finish = true;
+          } else if (++probe[e] >= tv.h) {
+            finish = true;
+          }
+          if (finish) {
+            out[idx[e]] = result;
+            active[e] = false;
+          }
+        }
+        act[e] = 0u;  // evaluated; the set's next reads are issued on its next refill
+      }
     }
-    if (finish) {
-      out[idx] = result;
-      active = false;
-    }
+    bool any = false;
+#pragma unroll
+    for (int s = 0; s < KPL; ++s) any |= active[s];
+    if (__ballot_sync(kFull, any) == 0u && sq.base + sq.head >= end) break;
   }
   if (COUNT) {
     probes = warp_sum(probes);
@@ -126,8 +198,74 @@ bucketed_find_kernel(TableView tv, const uint32_t *__restrict__ queries, uint32_
 }
 
 // ----------------------------------------------------------------------------
-// Bucketed build. Per-lane state machine; every round reads one bucket per
-// active key, then issues at most one atomic per lane.
+// Key and value streams of a build, read like StreamQueue, 32 pairs at a
+// time, two chunks ahead. Chunks are either consecutive pieces of the warp's
+// static slice, or (dynamic mode) claimed from a global cursor so that all
+// warps advance through the input together -- which keeps the in-flight
+// inserts of a grouped build inside a small window of the table.
+struct PairQueue {
+  uint64_t ba, bb, bc;  // input index of entry 0 of chunks a, b, c (warp-uniform)
+  int head;             // next unused entry of chunk a
+  uint32_t ka, kb, kc, va, vb, vc;
+};
+
+__device__ __forceinline__ uint64_t claim_chunk(Ctrl *ctrl, int lane) {
+  unsigned long long x = 0ull;
+  if (lane == 0) x = atomicAdd(&ctrl->work_cursor, 32ull);
+  return __shfl_sync(kFull, x, 0);
+}
+
+__device__ __forceinline__ void pair_init(PairQueue &q, const uint32_t *__restrict__ k, const uint32_t *__restrict__ v,
+                                          uint64_t beg, uint64_t end, bool dynamic, Ctrl *ctrl, int lane) {
+  if (dynamic) {
+    q.ba = claim_chunk(ctrl, lane);
+    q.bb = claim_chunk(ctrl, lane);
+    q.bc = claim_chunk(ctrl, lane);
+  } else {
+    q.ba = beg;
+    q.bb = beg + 32;
+    q.bc = beg + 64;
+  }
+  q.head = 0;
+  q.ka = stream_load(k, q.ba + lane, end);
+  q.kb = stream_load(k, q.bb + lane, end);
+  q.kc = stream_load(k, q.bc + lane, end);
+  q.va = stream_load(v, q.ba + lane, end);
+  q.vb = stream_load(v, q.bb + lane, end);
+  q.vc = stream_load(v, q.bc + lane, end);
+}
+
+__device__ __forceinline__ bool pair_exhausted(const PairQueue &q, uint64_t end) { return q.ba + q.head >= end; }
+
+__device__ __forceinline__ uint64_t pair_take(PairQueue &q, const uint32_t *__restrict__ k,
+                                              const uint32_t *__restrict__ v, uint64_t end, bool dynamic,
+                                              Ctrl *ctrl, unsigned need, unsigned below, int lane,
+                                              uint32_t &key, uint32_t &val) {
+  const int pos = q.head + __popc(need & below);
+  const uint32_t ka = __shfl_sync(kFull, q.ka, pos & 31), kb = __shfl_sync(kFull, q.kb, pos & 31);
+  const uint32_t va = __shfl_sync(kFull, q.va, pos & 31), vb = __shfl_sync(kFull, q.vb, pos & 31);
+  key = pos < 32 ? ka : kb;
+  val = pos < 32 ? va : vb;
+  const uint64_t at = pos < 32 ? q.ba + (uint64_t)pos : q.bb + (uint64_t)(pos - 32);
+  q.head += __popc(need);
+  if (q.head >= 32) {
+    q.head -= 32;
+    q.ba = q.bb;
+    q.bb = q.bc;
+    q.bc = dynamic ? claim_chunk(ctrl, lane) : q.bc + 32;
+    q.ka = q.kb;
+    q.kb = q.kc;
+    q.va = q.vb;
+    q.vb = q.vc;
+    q.kc = stream_load(k, q.bc + lane, end);
+    q.vc = stream_load(v, q.bc + lane, end);
+  }
+  return ((need >> lane) & 1u) ? at : ~0ull;
+}
+
+// ----------------------------------------------------------------------------
+// Bucketed build. Per-lane state machine; every turn of a slot reads one
+// bucket per active key, then issues at most one atomic per lane.
 //   BCHT (Sec. III-A, V-B): CAS into an empty slot of the current bucket; if
 //     it is full, exchange with a random slot (xorshift) and continue with the
 //     evicted pair at H_{(i+1) mod h}, i the lowest index with H_i equal to the
@@ -144,35 +282,54 @@ bucketed_find_kernel(TableView tv, const uint32_t *__restrict__ queries, uint32_
 //     bucket and continue with the evicted pair.
 // A failed CAS means the slot was taken, so the owner re-reads (a "retry";
 // each failure removes one empty slot for good, which bounds the retries).
-template <int SCHEME, int B, int G, bool COUNT>
+//
+// Each lane runs KPL independent slots. A slot's atomic result is inspected
+// only on the slot's next turn, so with KPL = 2 its latency is hidden behind
+// the other slot's bucket reads. per_warp = 0 selects dynamic chunks.
+template <int SCHEME, int B, int G, int KPL, bool COUNT>
 __global__ void __launch_bounds__(256)
 bucketed_insert_kernel(TableView tv, const uint32_t *__restrict__ keys,
                        const uint32_t *__restrict__ values, uint64_t n, uint64_t per_warp) {
   constexpr int PPL = B / G;
-  static_assert(B % G == 0 && 32 % G == 0 && PPL >= 1, "tile shape");
+  static_assert(B % G == 0 && 32 % G == 0 && PPL >= 1 && (KPL == 1 || KPL == 2), "tile shape");
   const int lane = threadIdx.x & 31;
   const int r = lane & (G - 1);
   const int tbase = lane - r;
   const unsigned tmask = (G == 32 ? kFull : ((1u << G) - 1u)) << tbase;
   const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t warp = gtid >> 5;
-  const uint64_t beg = warp * per_warp;
+  const bool dynamic = per_warp == 0;
+  const uint64_t beg = dynamic ? 0 : warp * per_warp;
   if (beg >= n) return;  // whole warp
-  const uint64_t end = beg + per_warp < n ? beg + per_warp : n;
+  const uint64_t end = dynamic ? n : (beg + per_warp < n ? beg + per_warp : n);
   const unsigned below = lanemask_lt();
   const int h = tv.h;
 
   uint32_t rng = lane_seed(tv.rng_seed, gtid);
-  uint64_t cursor = beg;
-  bool active = false, retrying = false;
-  uint64_t pair = 0;
-  uint32_t cur = 0, chain = 0, steps = 0, round = 0;
-  int phase = 0;
+  PairQueue pq;
+  pair_init(pq, keys, values, beg, end, dynamic, tv.ctrl, lane);
+  // per-slot state
+  bool active[KPL], retrying[KPL];
+  uint64_t pair[KPL], old[KPL];
+  uint32_t cur[KPL], chain[KPL], steps[KPL];
+  int op[KPL], phase[KPL];
   // remembered reads: P2BHT (l_a, s_a, b_a) = H_0; IHT a = primary, b = H_s0;
   // BCHT_LB best candidate so far in (l_a, s_a, b_a) and `from` in b_b
-  int l_a = 0, s_a = -1, l_b = 0, s_b = -1;
-  uint32_t b_a = 0, b_b = 0xFFFFFFFFu;
+  int l_a[KPL], s_a[KPL], l_b[KPL], s_b[KPL];
+  uint32_t b_a[KPL], b_b[KPL];
+#pragma unroll
+  for (int s = 0; s < KPL; ++s) {
+    active[s] = retrying[s] = false;
+    pair[s] = old[s] = 0;
+    cur[s] = chain[s] = steps[s] = 0;
+    op[s] = phase[s] = 0;
+    l_a[s] = l_b[s] = 0;
+    s_a[s] = s_b[s] = -1;
+    b_a[s] = 0;
+    b_b[s] = 0xFFFFFFFFu;
+  }
   unsigned long long probes = 0, retries = 0, evictions = 0, longest = 0;
+  uint32_t round = 0;
 
   for (;;) {
     if ((++round & 15u) == 0u) {  // leave early once the build has failed anywhere
@@ -180,187 +337,191 @@ bucketed_insert_kernel(TableView tv, const uint32_t *__restrict__ keys,
       st = __shfl_sync(kFull, st, 0);
       if (st & (kStatusBuildFailed | kStatusTimeout | kStatusCorrupt)) break;
     }
-    const unsigned need = __ballot_sync(kFull, !active);
-    if (need != 0u && cursor < end) {
-      const uint64_t mine = cursor + __popc(need & below);
-      if (!active && mine < end) {
-        const uint32_t k = __ldg(keys + mine);
-        if (k == kEmptyKey) {
-          atomicOr(&tv.ctrl->status, kStatusSentinel);
-        } else {
-          pair = ((uint64_t)__ldg(values + mine) << 32) | k;
-          active = true;
-          retrying = false;
-          chain = 0;
-          steps = 0;
-          phase = 0;
-          b_b = 0xFFFFFFFFu;
-          l_a = B + 1;
-          cur = bucket_of(tv.hf, 0, k);
-        }
-      }
-      cursor += __popc(need);
-      if (cursor > end) cursor = end;
-    }
-    const unsigned act = __ballot_sync(kFull, active);
-    if (act == 0u) {
-      if (cursor >= end) break;
-      continue;
-    }
-
-    // gather one bucket per active lane of the tile
-    uint64_t v[G][PPL];
 #pragma unroll
-    for (int j = 0; j < G; ++j) {
-      const uint32_t bj = __shfl_sync(kFull, cur, tbase + j);
-      if ((act >> (tbase + j)) & 1u) load_part_rw<PPL>(tv.slots + (uint64_t)bj * B, r, v[j]);
-    }
-    // owner learns how many slots are empty and where one of them is
-    int my_empty = 0, my_slot = -1;
-#pragma unroll
-    for (int j = 0; j < G; ++j) {
-      const bool aj = (act >> (tbase + j)) & 1u;
-      int cnt = 0, slot = -1;
-#pragma unroll
-      for (int p = 0; p < PPL; ++p) {
-        const unsigned em = __ballot_sync(kFull, aj && pair_key(v[j][p]) == kEmptyKey) & tmask;
-        cnt += __popc(em);
-        if (slot < 0 && em) slot = (__ffs(em) - 1 - tbase) * PPL + p;
-      }
-      if (lane == tbase + j) {
-        my_empty = cnt;
-        my_slot = slot;
-      }
-    }
-
-    int op = 0;  // 1 = CAS, 2 = exchange
-    uint64_t *target = nullptr;
-    if (active) {
-      if (COUNT) {
-        if (retrying) retries++;
-        else probes++;
-      }
-      const int load = B - my_empty;
-      const uint32_t k = pair_key(pair);
-      bool fail = false;
-      if (++steps > tv.max_steps) {
-        atomicOr(&tv.ctrl->status, kStatusTimeout);
-        active = false;
-      } else if (SCHEME == kBCHT) {
-        if (load < B) {
-          op = 1;
-          target = tv.slots + (uint64_t)cur * B + my_slot;
-        } else if (chain >= tv.max_chain) {
-          fail = true;
+    for (int s = 0; s < KPL; ++s) {
+      // -- resolve the atomic this slot issued on its previous turn
+      if (op[s] == 1) {
+        if (old[s] == kEmptyPair) {
+          active[s] = false;  // stored
+          if (COUNT && chain[s] > longest) longest = chain[s];
         } else {
-          op = 2;
-          target = tv.slots + (uint64_t)cur * B + (xorshift32(rng) % B);
-        }
-      } else if (SCHEME == kP2BHT) {
-        if (phase == 0) {
-          l_a = load; s_a = my_slot; b_a = cur;
-          phase = 1;
-          cur = bucket_of(tv.hf, 1, k);
-        } else if (l_a == B && load == B) {
-          fail = true;
-        } else {
-          op = 1;
-          target = (l_a <= load) ? tv.slots + (uint64_t)b_a * B + s_a
-                                 : tv.slots + (uint64_t)cur * B + my_slot;
-        }
-      } else if (SCHEME == kIHT) {
-        if (phase == 0) {
-          l_a = load; s_a = my_slot; b_a = cur;
-          if (load + 1 < tv.t) {
-            op = 1;
-            target = tv.slots + (uint64_t)cur * B + my_slot;
-          } else {
-            phase = 1;
-            cur = bucket_of(tv.hf, 1, k);
+          retrying[s] = true;  // slot taken since the read: read again
+          if (SCHEME == kP2BHT || SCHEME == kIHT || SCHEME == kBCHT_LB) {
+            phase[s] = 0;
+            l_a[s] = B + 1;
+            cur[s] = bucket_of(tv.hf, 0, pair_key(pair[s]));
           }
-        } else if (phase == 1) {
-          l_b = load; s_b = my_slot; b_b = cur;
-          phase = 2;
-          cur = bucket_of(tv.hf, 2, k);
-        } else if (l_b < B || load < B) {
-          op = 1;
-          target = (l_b <= load) ? tv.slots + (uint64_t)b_b * B + s_b
-                                 : tv.slots + (uint64_t)cur * B + my_slot;
-        } else if (l_a < B) {
-          op = 1;
-          target = tv.slots + (uint64_t)b_a * B + s_a;
-        } else {
-          fail = true;
         }
-      } else {  // kBCHT_LB
-        if (cur != b_b && load < l_a) {
-          l_a = load; s_a = my_slot; b_a = cur;
-        }
-        if (phase + 1 < h) {
-          phase++;
-          cur = bucket_of(tv.hf, phase, k);
-        } else if (l_a < B) {
-          op = 1;
-          target = tv.slots + (uint64_t)b_a * B + s_a;
-        } else if (l_a > B || chain >= tv.max_chain) {
-          fail = true;  // no candidate besides the one it came from, or chain bound
-        } else {
-          op = 2;
-          target = tv.slots + (uint64_t)b_a * B + (xorshift32(rng) % B);
-        }
-      }
-      if (fail) {
-        atomicOr(&tv.ctrl->status, kStatusBuildFailed);
-        active = false;
-        if (COUNT && chain > longest) longest = chain;
-      }
-    }
-
-    // at most one atomic per lane; a warp issues them together
-    uint64_t old = 0;
-    if (op == 1) old = cas_pair(target, kEmptyPair, pair);
-    else if (op == 2) old = exch_pair(target, pair);
-    if (op != 0) retrying = false;
-
-    if (op == 1) {
-      if (old == kEmptyPair) {
-        active = false;  // stored
-        if (COUNT && chain > longest) longest = chain;
-      } else {
-        retrying = true;  // slot taken since the read: read again
-        if (SCHEME == kP2BHT || SCHEME == kIHT || SCHEME == kBCHT_LB) {
-          phase = 0;
-          l_a = B + 1;
-          cur = bucket_of(tv.hf, 0, pair_key(pair));
-        }
-      }
-    } else if (op == 2) {
-      if (COUNT) evictions++;
-      chain++;
-      if (pair_key(old) == kEmptyKey) {
-        active = false;  // the slot had been emptied -- cannot happen, but storing is complete
-      } else if (SCHEME == kBCHT) {
-        const uint32_t from = cur;
-        pair = old;
-        const uint32_t k = pair_key(old);
-        int i = -1;
+      } else if (op[s] == 2) {
+        if (COUNT) evictions++;
+        chain[s]++;
+        if (pair_key(old[s]) == kEmptyKey) {
+          active[s] = false;  // the slot had been emptied -- cannot happen, but storing is complete
+        } else if (SCHEME == kBCHT) {
+          const uint32_t from = cur[s];
+          pair[s] = old[s];
+          const uint32_t k = pair_key(old[s]);
+          int i = -1;
 #pragma unroll
-        for (int f = 0; f < 4; ++f)
-          if (f < h && i < 0 && bucket_of(tv.hf, f, k) == from) i = f;
-        if (i < 0) {
-          atomicOr(&tv.ctrl->status, kStatusCorrupt);
-          active = false;
-        } else {
-          cur = bucket_of(tv.hf, (i + 1) % h, k);
+          for (int f = 0; f < 4; ++f)
+            if (f < h && i < 0 && bucket_of(tv.hf, f, k) == from) i = f;
+          if (i < 0) {
+            atomicOr(&tv.ctrl->status, kStatusCorrupt);
+            active[s] = false;
+          } else {
+            cur[s] = bucket_of(tv.hf, (i + 1) % h, k);
+          }
+        } else {  // kBCHT_LB: evicted pair restarts its candidate scan, excluding b_a
+          pair[s] = old[s];
+          b_b[s] = b_a[s];
+          phase[s] = 0;
+          l_a[s] = B + 1;
+          cur[s] = bucket_of(tv.hf, 0, pair_key(old[s]));
         }
-      } else {  // kBCHT_LB: evicted pair restarts its candidate scan, excluding b_a
-        pair = old;
-        b_b = b_a;
-        phase = 0;
-        l_a = B + 1;
-        cur = bucket_of(tv.hf, 0, pair_key(old));
       }
+      op[s] = 0;
+
+      // -- refill
+      const unsigned need = __ballot_sync(kFull, !active[s]);
+      if (need != 0u && !pair_exhausted(pq, end)) {
+        uint32_t k, val;
+        const uint64_t at = pair_take(pq, keys, values, end, dynamic, tv.ctrl, need, below, lane, k, val);
+        if (at < end) {
+          if (k == kEmptyKey) {
+            atomicOr(&tv.ctrl->status, kStatusSentinel);
+          } else {
+            pair[s] = ((uint64_t)val << 32) | k;
+            active[s] = true;
+            retrying[s] = false;
+            chain[s] = 0;
+            steps[s] = 0;
+            phase[s] = 0;
+            b_b[s] = 0xFFFFFFFFu;
+            l_a[s] = B + 1;
+            cur[s] = bucket_of(tv.hf, 0, k);
+          }
+        }
+      }
+      const unsigned act = __ballot_sync(kFull, active[s]);
+      if (act == 0u) continue;
+
+      // -- gather one bucket per active lane of the tile
+      uint64_t v[G][PPL];
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        const uint32_t bj = __shfl_sync(kFull, cur[s], tbase + j);
+        if ((act >> (tbase + j)) & 1u) load_part_rw<PPL>(tv.slots + (uint64_t)bj * B, r, v[j]);
+      }
+      // owner learns how many slots are empty and where one of them is
+      int my_empty = 0, my_slot = -1;
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        const bool aj = (act >> (tbase + j)) & 1u;
+        int cnt = 0, slot = -1;
+#pragma unroll
+        for (int p = 0; p < PPL; ++p) {
+          const unsigned em = __ballot_sync(kFull, aj && pair_key(v[j][p]) == kEmptyKey) & tmask;
+          cnt += __popc(em);
+          if (slot < 0 && em) slot = (__ffs(em) - 1 - tbase) * PPL + p;
+        }
+        if (lane == tbase + j) {
+          my_empty = cnt;
+          my_slot = slot;
+        }
+      }
+
+      // -- decide and issue this slot's atomic
+      uint64_t *target = nullptr;
+      if (active[s]) {
+        if (COUNT) {
+          if (retrying[s]) retries++;
+          else probes++;
+        }
+        const int load = B - my_empty;
+        const uint32_t k = pair_key(pair[s]);
+        bool fail = false;
+        if (++steps[s] > tv.max_steps) {
+          atomicOr(&tv.ctrl->status, kStatusTimeout);
+          active[s] = false;
+        } else if (SCHEME == kBCHT) {
+          if (load < B) {
+            op[s] = 1;
+            target = tv.slots + (uint64_t)cur[s] * B + my_slot;
+          } else if (chain[s] >= tv.max_chain) {
+            fail = true;
+          } else {
+            op[s] = 2;
+            target = tv.slots + (uint64_t)cur[s] * B + (xorshift32(rng) % B);
+          }
+        } else if (SCHEME == kP2BHT) {
+          if (phase[s] == 0) {
+            l_a[s] = load; s_a[s] = my_slot; b_a[s] = cur[s];
+            phase[s] = 1;
+            cur[s] = bucket_of(tv.hf, 1, k);
+          } else if (l_a[s] == B && load == B) {
+            fail = true;
+          } else {
+            op[s] = 1;
+            target = (l_a[s] <= load) ? tv.slots + (uint64_t)b_a[s] * B + s_a[s]
+                                      : tv.slots + (uint64_t)cur[s] * B + my_slot;
+          }
+        } else if (SCHEME == kIHT) {
+          if (phase[s] == 0) {
+            l_a[s] = load; s_a[s] = my_slot; b_a[s] = cur[s];
+            if (load + 1 < tv.t) {
+              op[s] = 1;
+              target = tv.slots + (uint64_t)cur[s] * B + my_slot;
+            } else {
+              phase[s] = 1;
+              cur[s] = bucket_of(tv.hf, 1, k);
+            }
+          } else if (phase[s] == 1) {
+            l_b[s] = load; s_b[s] = my_slot; b_b[s] = cur[s];
+            phase[s] = 2;
+            cur[s] = bucket_of(tv.hf, 2, k);
+          } else if (l_b[s] < B || load < B) {
+            op[s] = 1;
+            target = (l_b[s] <= load) ? tv.slots + (uint64_t)b_b[s] * B + s_b[s]
+                                      : tv.slots + (uint64_t)cur[s] * B + my_slot;
+          } else if (l_a[s] < B) {
+            op[s] = 1;
+            target = tv.slots + (uint64_t)b_a[s] * B + s_a[s];
+          } else {
+            fail = true;
+          }
+        } else {  // kBCHT_LB
+          if (cur[s] != b_b[s] && load < l_a[s]) {
+            l_a[s] = load; s_a[s] = my_slot; b_a[s] = cur[s];
+          }
+          if (phase[s] + 1 < h) {
+            phase[s]++;
+            cur[s] = bucket_of(tv.hf, phase[s], k);
+          } else if (l_a[s] < B) {
+            op[s] = 1;
+            target = tv.slots + (uint64_t)b_a[s] * B + s_a[s];
+          } else if (l_a[s] > B || chain[s] >= tv.max_chain) {
+            fail = true;  // no candidate besides the one it came from, or chain bound
+          } else {
+            op[s] = 2;
+            target = tv.slots + (uint64_t)b_a[s] * B + (xorshift32(rng) % B);
+          }
+        }
+        if (fail) {
+          atomicOr(&tv.ctrl->status, kStatusBuildFailed);
+          active[s] = false;
+          if (COUNT && chain[s] > longest) longest = chain[s];
+        }
+      }
+      // at most one atomic per lane; a warp issues them together and the
+      // results are read on the slot's next turn
+      if (op[s] == 1) old[s] = cas_pair(target, kEmptyPair, pair[s]);
+      else if (op[s] == 2) old[s] = exch_pair(target, pair[s]);
+      if (op[s] != 0) retrying[s] = false;
     }
+    bool any = false;
+#pragma unroll
+    for (int s = 0; s < KPL; ++s) any |= active[s];
+    if (__ballot_sync(kFull, any) == 0u && pair_exhausted(pq, end)) break;
   }
   if (COUNT) {
     probes = warp_sum(probes);

@@ -1,0 +1,137 @@
+// kern_group.cu -- grouping of the input pairs by first-choice bucket range
+// before a build (a GB300 locality measure, not part of the paper's method,
+// which may insert keys in any order).
+//
+// A random insert touches a 128-byte bucket line that has usually left the
+// L2 since the previous insert into it, so every insert pays a DRAM line read
+// plus a partial-line write-back. Grouping the pairs by H_0(k) >> shift and
+// inserting the groups in order keeps the in-flight inserts inside a window
+// of a few MB of the table, whose lines then stay in L2 while they fill up.
+#include "ght_internal.h"
+#include "ght_kernels.cuh"
+
+namespace ght {
+
+__device__ __forceinline__ uint32_t group_of(const TableView &tv, uint32_t k, int shift) {
+  return k == kEmptyKey ? 0u : (bucket_of(tv.hf, 0, k) >> shift);  // sentinels are flagged by the insert
+}
+
+// Pass 1: per-group counts (block-local histogram in shared memory).
+__global__ void __launch_bounds__(256)
+group_count_kernel(TableView tv, const uint32_t *__restrict__ keys, uint64_t n, int shift, uint32_t groups,
+                   uint32_t *__restrict__ counts) {
+  extern __shared__ uint32_t sh[];
+  for (uint32_t i = threadIdx.x; i < groups; i += blockDim.x) sh[i] = 0u;
+  __syncthreads();
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    atomicAdd(&sh[group_of(tv, __ldg(keys + i), shift)], 1u);
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < groups; i += blockDim.x)
+    if (sh[i]) atomicAdd(&counts[i], sh[i]);
+}
+
+// Exclusive prefix sum of the counts into the cursors (one block).
+__global__ void __launch_bounds__(1024)
+group_scan_kernel(const uint32_t *__restrict__ counts, uint32_t groups, uint32_t *__restrict__ cursors) {
+  __shared__ uint32_t warp_tot[32];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0u;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (uint32_t base = 0; base < groups; base += blockDim.x) {
+    const uint32_t i = base + threadIdx.x;
+    const uint32_t x = i < groups ? counts[i] : 0u;
+    uint32_t incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      uint32_t t = warp_tot[lane];
+      uint32_t ti = t;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, ti, o);
+        if (lane >= o) ti += y;
+      }
+      warp_tot[lane] = ti - t;  // exclusive warp offsets
+    }
+    __syncthreads();
+    if (i < groups) cursors[i] = carry + warp_tot[wid] + incl - x;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry += warp_tot[wid] + incl;
+    __syncthreads();
+  }
+}
+
+// Pass 2: scatter pairs to their group. Each block takes a tile of
+// kGroupTile pairs, ranks them per group in shared memory, reserves one
+// range per non-empty group with a single global atomic, then writes; the
+// pairs of a group within a tile land contiguously.
+constexpr int kGroupPerThread = 16;
+constexpr int kGroupTile = 256 * kGroupPerThread;
+
+__global__ void __launch_bounds__(256)
+group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint32_t *__restrict__ values,
+                     uint64_t n, int shift, uint32_t groups, uint32_t *__restrict__ cursors,
+                     uint32_t *__restrict__ out_k, uint32_t *__restrict__ out_v) {
+  extern __shared__ uint32_t sh[];
+  uint32_t *cnt = sh, *base = sh + groups;
+  for (uint64_t t0 = (uint64_t)blockIdx.x * kGroupTile; t0 < n; t0 += (uint64_t)gridDim.x * kGroupTile) {
+    for (uint32_t i = threadIdx.x; i < groups; i += blockDim.x) cnt[i] = 0u;
+    __syncthreads();
+    uint32_t k[kGroupPerThread], v[kGroupPerThread], g[kGroupPerThread], rank[kGroupPerThread];
+#pragma unroll
+    for (int u = 0; u < kGroupPerThread; ++u) {
+      const uint64_t i = t0 + (uint64_t)u * blockDim.x + threadIdx.x;  // coalesced reads
+      if (i < n) {
+        k[u] = __ldg(keys + i);
+        v[u] = __ldg(values + i);
+        g[u] = group_of(tv, k[u], shift);
+        rank[u] = atomicAdd(&cnt[g[u]], 1u);
+      }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < groups; i += blockDim.x)
+      if (cnt[i]) base[i] = atomicAdd(&cursors[i], cnt[i]);
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kGroupPerThread; ++u) {
+      const uint64_t i = t0 + (uint64_t)u * blockDim.x + threadIdx.x;
+      if (i < n) {
+        const uint32_t at = base[g[u]] + rank[u];
+        out_k[at] = k[u];
+        out_v[at] = v[u];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_group(const TableView &tv, const uint32_t *keys, const uint32_t *values, uint64_t n,
+                         int shift, uint32_t groups, uint32_t *counts, uint32_t *cursors, uint32_t *out_k,
+                         uint32_t *out_v, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  if (n > 0xFFFFFFFFull || groups == 0 || groups > kMaxGroups) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(counts, 0, groups * sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  int blocks = 0;
+  e = grid_for(group_count_kernel, n, 0, &blocks);
+  if (e != cudaSuccess) return e;
+  group_count_kernel<<<blocks, 256, groups * sizeof(uint32_t), s>>>(tv, keys, n, shift, groups, counts);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  group_scan_kernel<<<1, 1024, 0, s>>>(counts, groups, cursors);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const uint64_t tiles = (n + kGroupTile - 1) / kGroupTile;
+  e = grid_for(group_scatter_kernel, tiles * 256, 0, &blocks);
+  if (e != cudaSuccess) return e;
+  group_scatter_kernel<<<blocks, 256, 2 * groups * sizeof(uint32_t), s>>>(tv, keys, values, n, shift, groups,
+                                                                         cursors, out_k, out_v);
+  return cudaGetLastError();
+}
+
+}  // namespace ght

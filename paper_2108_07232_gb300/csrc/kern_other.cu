@@ -30,26 +30,38 @@ __global__ void hash_kernel(TableView tv, const uint32_t *__restrict__ keys, uin
   }
 }
 
-template <int S, int B, int G>
-static cudaError_t insert_shape(const TableView &tv, const uint32_t *k, const uint32_t *v,
-                                uint64_t n, const LaunchOpts &o, cudaStream_t s) {
-  auto kern = o.count ? bucketed_insert_kernel<S, B, G, true> : bucketed_insert_kernel<S, B, G, false>;
+template <int S, int B, int G, int KPL>
+static cudaError_t insert_kpl(const TableView &tv, const uint32_t *k, const uint32_t *v,
+                              uint64_t n, const LaunchOpts &o, cudaStream_t s) {
+  auto kern = o.count ? bucketed_insert_kernel<S, B, G, KPL, true> : bucketed_insert_kernel<S, B, G, KPL, false>;
   int blocks = 0;
   cudaError_t e = grid_for(kern, n, o.blocks_per_sm, &blocks);
   if (e != cudaSuccess) return e;
-  kern<<<blocks, kThreads, 0, s>>>(tv, k, v, n, per_warp_of(n, blocks));
+  kern<<<blocks, kThreads, 0, s>>>(tv, k, v, n, o.dynamic ? 0 : per_warp_of(n, blocks));
+  return cudaGetLastError();
+}
+
+template <int S, int B, int G>
+static cudaError_t insert_shape(const TableView &tv, const uint32_t *k, const uint32_t *v,
+                                uint64_t n, const LaunchOpts &o, cudaStream_t s) {
+  return o.keys_per_lane == 1 ? insert_kpl<S, B, G, 1>(tv, k, v, n, o, s) : insert_kpl<S, B, G, 2>(tv, k, v, n, o, s);
+}
+
+template <int S, int B, int G, int KPL>
+static cudaError_t find_kpl(const TableView &tv, const uint32_t *q, uint32_t *out, uint64_t n,
+                            const LaunchOpts &o, cudaStream_t s) {
+  auto kern = o.count ? bucketed_find_kernel<S, B, G, KPL, true> : bucketed_find_kernel<S, B, G, KPL, false>;
+  int blocks = 0;
+  cudaError_t e = grid_for(kern, n, o.blocks_per_sm, &blocks);
+  if (e != cudaSuccess) return e;
+  kern<<<blocks, kThreads, 0, s>>>(tv, q, out, n, per_warp_of(n, blocks));
   return cudaGetLastError();
 }
 
 template <int S, int B, int G>
 static cudaError_t find_shape(const TableView &tv, const uint32_t *q, uint32_t *out, uint64_t n,
                               const LaunchOpts &o, cudaStream_t s) {
-  auto kern = o.count ? bucketed_find_kernel<S, B, G, true> : bucketed_find_kernel<S, B, G, false>;
-  int blocks = 0;
-  cudaError_t e = grid_for(kern, n, o.blocks_per_sm, &blocks);
-  if (e != cudaSuccess) return e;
-  kern<<<blocks, kThreads, 0, s>>>(tv, q, out, n, per_warp_of(n, blocks));
-  return cudaGetLastError();
+  return o.keys_per_lane == 1 ? find_kpl<S, B, G, 1>(tv, q, out, n, o, s) : find_kpl<S, B, G, 2>(tv, q, out, n, o, s);
 }
 
 bool other_shape_supported(int scheme, int B, int G) {

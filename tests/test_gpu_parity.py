@@ -109,9 +109,12 @@ def test_insert_probes_match_sequential_oracle(G, scheme, lf, tol):
     (O.P2BHT, 32, 8, 0.9), (O.IHT, 32, 8, 0.9), (O.BCHT_LB, 32, 8, 0.97),
 ])
 def test_tile_shapes_and_wide_buckets(G, scheme, b, lanes, lf):
-    t, keys, vals = build_table(G, scheme, N_SMALL, lf, bucket_size=b, tile_lanes=lanes)
+    kpl = 1 + (lanes % 3 == 1)  # vary the keys kept in flight per lane too
+    t, keys, vals = build_table(G, scheme, N_SMALL, lf, bucket_size=b, tile_lanes=lanes,
+                                build_tile_lanes=lanes, keys_per_lane=kpl, build_keys_per_lane=3 - kpl)
     st = t.stats()
-    assert st["bucket_size"] == b and st["tile_lanes"] == lanes
+    assert st["bucket_size"] == b and st["tile_lanes"] == lanes and st["build_tile_lanes"] == lanes
+    assert st["keys_per_lane"] == kpl and st["build_keys_per_lane"] == 3 - kpl
     if scheme == O.IHT:
         assert st["threshold"] == 26  # ceil(0.8 * 32)
     T = oracle_view(st, scheme, N_SMALL, lf)
@@ -123,6 +126,43 @@ def test_tile_shapes_and_wide_buckets(G, scheme, b, lanes, lf):
     got = t.find(q.cuda()).cpu()
     assert (O._u32(got) == O.lookup(keys, vals, q)).all()
     assert t.stats()["find_probes"] == T.find(q, slots=slots)[2]
+
+
+@pytest.mark.parametrize("scheme,lf", [(O.BCHT, 0.99), (O.BCHT, 0.9), (O.P2BHT, 0.8), (O.IHT, 0.86),
+                                       (O.BCHT_LB, 0.95)])
+@pytest.mark.parametrize("lanes", [8, 16])
+def test_grouped_build_parity(G, scheme, lf, lanes):
+    """Builds that first regroup the pairs by first-choice bucket range
+    (forced on at this size) give a valid table with bit-exact finds."""
+    if lanes == 16 and scheme != O.BCHT:
+        pytest.skip("16-lane tiles are instantiated for BCHT only")
+    t, keys, vals = build_table(G, scheme, N_SMALL, lf, group_build=1, build_tile_lanes=lanes)
+    st = t.stats()
+    assert st["last_build_grouped"] == 1 and st["built"] == 1
+    T = oracle_view(st, scheme, N_SMALL, lf)
+    slots = t.export()
+    ok, msg = T.validate(keys, vals, slots=slots)
+    assert ok, msg
+    q = W.make_queries(keys, NQ_SMALL, 0.5, seed=12)
+    t.reset_counters()
+    assert (O._u32(t.find(q.cuda()).cpu()) == O.lookup(keys, vals, q)).all()
+    assert t.stats()["find_probes"] == T.find(q, slots=slots)[2]
+
+
+def test_grouped_build_rejects_sentinel_and_falls_back_without_scratch(G):
+    bad = W.make_keys(5000, 3)
+    bad[1234] = -1
+    t = G.HashTable("bcht", 5000, 0.9, seed=1, group_build=1)
+    with pytest.raises(G.GhtError) as e:
+        t.build(bad.cuda(), bad.cuda())
+    assert e.value.status == "GHT_ERR_SENTINEL_KEY"
+    # caller storage without scratch: the build runs ungrouped and still succeeds
+    keys, vals = W.make_keys(5000, 4), W.make_values(5000, 4)
+    t = G.HashTable("bcht", 5000, 0.9, seed=1, group_build=1)
+    t._ensure_scratch = lambda n: None
+    t.build(keys.cuda(), vals.cuda())
+    assert t.stats()["last_build_grouped"] == 0
+    assert torch.equal(t.find(keys.cuda()).cpu(), vals)
 
 
 def test_device_hash_matches_oracle(G):
