@@ -167,6 +167,30 @@ int ght_find(const ght_table *t, const uint32_t *d_queries, uint32_t *d_out, uin
 int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_values, uint64_t n);
 int ght_find_host(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out, uint64_t n);
 
+/* Host-buffer find that allocates nothing. This paper has no counterpart to
+ * it: it exists for callers that must not call the CUDA allocator once they
+ * run -- for example an inference-server plugin whose execute step may not
+ * allocate, or code that runs while another memory pool owns the device
+ * memory -- and that would otherwise need ght_find_host, whose device
+ * staging buffers are allocated per call.
+ *
+ * The queries are copied into a staging array that is part of the library
+ * image (a static device array of 2 x GHT_NOALLOC_MAX_QUERIES uint32, 32 MiB,
+ * held on every GPU that loads the library until the process exits), found
+ * there by the ordinary find kernel, and the results are copied back into
+ * h_out before the call returns. n must not exceed GHT_NOALLOC_MAX_QUERIES
+ * (else GHT_ERR_CAPACITY, nothing is done); n = 0 is a no-op. The table must
+ * have been built and its device must be current.
+ *
+ * The first call on a device looks up the staging array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call on a device shares the one staging array, whose contents are
+ * whatever the last call left there: calls that overlap on the GPU (from
+ * several host threads or streams at once) race on it and must be
+ * serialised by the caller. */
+#define GHT_NOALLOC_MAX_QUERIES (1u << 22)
+int ght_find_host_noalloc(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out, uint64_t n);
+
 /* Device scratch a build of n keys uses for grouping (0 if this table
  * builds without grouping). */
 uint64_t ght_build_scratch_bytes(const ght_table *t, uint64_t n);

@@ -15,9 +15,9 @@ from __future__ import annotations
 from ._binding import (  # noqa: F401
     BCHT, BCHT_LB, CUCKOO1, EMPTY, IHT, P2BHT, SCHEMES, GhtConfig, GhtError, GhtStats, HashTable,
     ght_build, ght_build_host, ght_create, ght_create_ex, ght_default_config, ght_destroy,
-    ght_export, ght_find, ght_find_host, ght_hash_device, ght_hash_host, ght_last_error,
+    ght_export, ght_find, ght_find_host, ght_find_host_noalloc, ght_hash_device, ght_hash_host, ght_last_error,
     ght_reset_counters, ght_set_stream, ght_stats, ght_table_bytes, ght_version, lib, lib_path,
-    ght_build_scratch_bytes, ght_set_build_scratch,
+    NOALLOC_MAX_QUERIES, ght_build_scratch_bytes, ght_set_build_scratch,
 )
 
 __all__ = [

@@ -91,6 +91,7 @@ def lib():
                 "ght_find": ([vp, vp, vp, u64], i32),
                 "ght_build_host": ([vp, vp, vp, u64], i32),
                 "ght_find_host": ([vp, vp, vp, u64], i32),
+                "ght_find_host_noalloc": ([vp, vp, vp, u64], i32),
                 "ght_stats": ([vp, C.POINTER(GhtStats)], i32),
                 "ght_build_scratch_bytes": ([vp, u64], u64),
                 "ght_set_build_scratch": ([vp, vp, u64], i32),
@@ -189,6 +190,13 @@ def ght_build_host(t: int, h_keys, h_values, n: int) -> None:
 
 def ght_find_host(t: int, h_queries, h_out, n: int) -> None:
     _check(lib().ght_find_host(t, _ptr(h_queries), _ptr(h_out), n))
+
+
+def ght_find_host_noalloc(t: int, h_queries, h_out, n: int) -> None:
+    _check(lib().ght_find_host_noalloc(t, _ptr(h_queries), _ptr(h_out), n))
+
+
+NOALLOC_MAX_QUERIES = 1 << 22
 
 
 def ght_build_scratch_bytes(t: int, n: int) -> int:

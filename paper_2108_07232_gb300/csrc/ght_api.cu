@@ -723,3 +723,55 @@ void ght_destroy(ght_table *t) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Host-buffer find without allocation (declared in ght.h). The staging array
+// is a file-scope device variable, so it exists as soon as the library's
+// device code is loaded on a GPU and no allocator is involved. In host code
+// the name g_noalloc_staging is only a host-side stand-in, so the device
+// address is looked up once per device and passed to the copies and kernel.
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) uint32_t g_noalloc_staging[2ull * GHT_NOALLOC_MAX_QUERIES];
+std::mutex g_noalloc_mu;
+uint32_t *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+}  // namespace
+
+extern "C" int ght_find_host_noalloc(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out,
+                                     uint64_t n) {
+  if (!t) return fail(GHT_ERR_INVALID_ARG, "table is NULL");
+  if (!t->built) return fail(GHT_ERR_NOT_BUILT, "table has no successful build");
+  if (n > GHT_NOALLOC_MAX_QUERIES)
+    return fail(GHT_ERR_CAPACITY, "n = %llu exceeds the %u queries the static staging array holds",
+                (unsigned long long)n, GHT_NOALLOC_MAX_QUERIES);
+  if (n == 0) return GHT_OK;
+  if (!h_queries || !h_out) return fail(GHT_ERR_INVALID_ARG, "queries or out is NULL");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "querying the current device");
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(GHT_ERR_INVALID_ARG, "device %d out of range", dev);
+  uint32_t *base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      // set-up, once per device, with that device current
+      void *p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_staging);
+      if (e != cudaSuccess) return cuda_fail(e, "looking up the static staging array");
+      g_noalloc_ptr[dev] = static_cast<uint32_t *>(p);
+    }
+    base = g_noalloc_ptr[dev];
+  }
+  uint32_t *d_q = base, *d_o = base + GHT_NOALLOC_MAX_QUERIES;
+  e = cudaMemcpyAsync(d_q, h_queries, n * sizeof(uint32_t), cudaMemcpyHostToDevice, t->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "copying queries to the staging array");
+  e = launch_find(t, d_q, d_o, n);
+  if (e != cudaSuccess) return cuda_fail(e, "launching find");
+  e = cudaMemcpyAsync(h_out, d_o, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, t->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "copying results back");
+  e = cudaEventRecord(t->done, t->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "recording an event");
+  return wait_event(t->done, wait_limit_seconds());
+}
