@@ -223,6 +223,79 @@ int ght_hash_host(uint32_t a, uint32_t c, uint32_t m, const uint32_t *h_keys, ui
 /* Release the table (and its storage, if library-owned). NULL is a no-op. */
 void ght_destroy(ght_table *t);
 
+/* ---------------------------------------------------------------------------
+ * Batched tables: many independent BCHT tables (b = 16, h = 3; Sec. III-A,
+ * V-B) built and queried by single launches instead of one build and one find
+ * per table. Not in the paper: it is the same per-table method, with the
+ * tables' work merged into shared launches, for workloads of many small or
+ * uneven tables.
+ *
+ * Inputs are concatenated over the tables: table t owns keys/values
+ * [key_offsets[t], key_offsets[t+1]) and queries/results
+ * [query_offsets[t], query_offsets[t+1]). Table t's hash constants come from
+ * seed + t * 0x9E3779B97F4A7C15 (mod 2^64) with the same derivation as a
+ * single table, per attempt.
+ * ------------------------------------------------------------------------- */
+typedef struct ght_batch ght_batch; /* opaque, library-owned */
+
+typedef struct {
+  uint32_t num_tables;
+  uint32_t tables_failed;      /* tables without a successful build after repair */
+  uint64_t total_keys, total_queries, total_slots, table_bytes;
+  uint32_t rebuilds;           /* per-table rebuilds with fresh constants in the last build or run */
+  int32_t tuned;               /* 1 after ght_batch_autotune */
+  int32_t tile_lanes, keys_per_lane;              /* find shape */
+  int32_t build_tile_lanes, build_keys_per_lane;  /* insert shape */
+  double last_run_ms;          /* device time of the last ght_batch_run graph launch */
+  uint64_t graph_launches;
+} ght_batch_stats_t;
+
+/* Create num_tables empty tables, table t sized for h_capacities[t] keys at
+ * h_load_factors[t] (Sec. III sizing), in one device allocation. cfg may be
+ * NULL (max_chain, max_attempts and the launch shapes apply). NULL on error. */
+ght_batch *ght_batch_create(uint32_t num_tables, const uint64_t *h_capacities, const double *h_load_factors,
+                            uint64_t seed, const ght_config *cfg);
+
+/* Issue later work on `cuda_stream` (NULL = legacy default stream). */
+int ght_batch_set_stream(ght_batch *b, void *cuda_stream);
+
+/* Set the input layout: num_tables + 1 non-decreasing offsets each, starting
+ * at 0; table t's key count may not exceed its capacity. Synchronous upload. */
+int ght_batch_set_layout(ght_batch *b, const uint64_t *h_key_offsets, const uint64_t *h_query_offsets);
+
+/* Build every table from the concatenated device arrays with one fill and
+ * one insert launch for the whole batch; reads the tables' status words
+ * once, then rebuilds each failed table alone with its next constants (up to
+ * max_attempts). GHT_ERR_BUILD_FAILED if any table stays unbuilt. */
+int ght_batch_build(ght_batch *b, const uint32_t *d_keys, const uint32_t *d_values);
+
+/* Find every table's queries with one launch (asynchronous). */
+int ght_batch_find(const ght_batch *b, const uint32_t *d_queries, uint32_t *d_out);
+
+/* Build and find in one CUDA-graph launch (fill, insert, find, status read
+ * back), captured on the first call and re-captured when the arrays or the
+ * launch shapes change; waits once. Tables whose build failed are rebuilt
+ * alone and their queries answered again before returning. The graph is
+ * launched on the batch's stream, which must not be capturing. */
+int ght_batch_run(ght_batch *b, const uint32_t *d_keys, const uint32_t *d_values, const uint32_t *d_queries,
+                  uint32_t *d_out);
+
+/* Choose the insert and find launch shapes (lanes per bucket tile, keys per
+ * lane) by timing each candidate on these arrays; keeps the fastest. The
+ * tables are rebuilt as a side effect. */
+int ght_batch_autotune(ght_batch *b, const uint32_t *d_keys, const uint32_t *d_values,
+                       const uint32_t *d_queries, uint32_t *d_out);
+
+int ght_batch_stats(const ght_batch *b, ght_batch_stats_t *out);
+
+/* Per-table view in the single-table stats format (shape, constants, n). */
+int ght_batch_table_stats(const ght_batch *b, uint32_t table, ght_stats_t *out);
+
+/* Copy table `table`'s slots to host memory (synchronous). */
+int ght_batch_export(const ght_batch *b, uint32_t table, uint64_t *h_slots, uint64_t n_slots);
+
+void ght_batch_destroy(ght_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

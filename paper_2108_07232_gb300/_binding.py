@@ -61,6 +61,19 @@ class GhtStats(C.Structure):
         return d
 
 
+class GhtBatchStats(C.Structure):
+    _fields_ = [
+        ("num_tables", C.c_uint32), ("tables_failed", C.c_uint32), ("total_keys", C.c_uint64),
+        ("total_queries", C.c_uint64), ("total_slots", C.c_uint64), ("table_bytes", C.c_uint64),
+        ("rebuilds", C.c_uint32), ("tuned", C.c_int32), ("tile_lanes", C.c_int32),
+        ("keys_per_lane", C.c_int32), ("build_tile_lanes", C.c_int32), ("build_keys_per_lane", C.c_int32),
+        ("last_run_ms", C.c_double), ("graph_launches", C.c_uint64),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -100,6 +113,17 @@ def lib():
                 "ght_hash_device": ([vp, vp, vp, u64], i32),
                 "ght_hash_host": ([u32, u32, u32, vp, vp, u64], i32),
                 "ght_destroy": ([vp], None),
+                "ght_batch_create": ([C.c_uint32, vp, vp, u64, C.POINTER(GhtConfig)], vp),
+                "ght_batch_set_stream": ([vp, vp], i32),
+                "ght_batch_set_layout": ([vp, vp, vp], i32),
+                "ght_batch_build": ([vp, vp, vp], i32),
+                "ght_batch_find": ([vp, vp, vp], i32),
+                "ght_batch_run": ([vp, vp, vp, vp, vp], i32),
+                "ght_batch_autotune": ([vp, vp, vp, vp, vp], i32),
+                "ght_batch_stats": ([vp, C.POINTER(GhtBatchStats)], i32),
+                "ght_batch_table_stats": ([vp, C.c_uint32, C.POINTER(GhtStats)], i32),
+                "ght_batch_export": ([vp, C.c_uint32, vp, u64], i32),
+                "ght_batch_destroy": ([vp], None),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -370,3 +394,106 @@ class HashTable:
 def _device_of(dev):
     import torch
     return torch.cuda.device(dev)
+
+
+# --- batched tables -------------------------------------------------------------
+
+class Batch:
+    """Many independent BCHT tables (b = 16, h = 3) built and queried by shared
+    launches. Inputs are concatenated int32 (uint32 bits) tensors with per-table
+    offsets set once by :meth:`set_layout`."""
+
+    def __init__(self, capacities, load_factors, seed: int = 0, device=None, **config):
+        import numpy as np
+        import torch
+
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        caps = np.ascontiguousarray(capacities, dtype=np.uint64)
+        lfs = np.ascontiguousarray(load_factors, dtype=np.float64)
+        if caps.size != lfs.size or caps.size == 0:
+            raise ValueError("capacities and load_factors must have the same non-zero length")
+        self.num_tables = int(caps.size)
+        cfg = _config(config) if config else None
+        with torch.cuda.device(self.device):
+            b = lib().ght_batch_create(self.num_tables, caps.ctypes.data, lfs.ctypes.data, seed,
+                                       C.byref(cfg) if cfg else None)
+        if not b:
+            raise GhtError(1, ght_last_error())
+        self._b = b
+        self.key_offsets = None
+        self.query_offsets = None
+
+    def close(self) -> None:
+        if getattr(self, "_b", None):
+            lib().ght_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self):
+        import torch
+        _check(lib().ght_batch_set_stream(self._b, torch.cuda.current_stream(self.device).cuda_stream))
+
+    def set_layout(self, key_offsets, query_offsets) -> None:
+        import numpy as np
+        ko = np.ascontiguousarray(key_offsets, dtype=np.uint64)
+        qo = np.ascontiguousarray(query_offsets, dtype=np.uint64)
+        if ko.size != self.num_tables + 1 or qo.size != self.num_tables + 1:
+            raise ValueError("offsets need num_tables + 1 entries")
+        _check(lib().ght_batch_set_layout(self._b, ko.ctypes.data, qo.ctypes.data))
+        self.key_offsets, self.query_offsets = ko, qo
+
+    def build(self, keys, values) -> None:
+        import torch
+        with torch.cuda.device(self.device):
+            self._stream()
+            _check(lib().ght_batch_build(self._b, _ptr(keys), _ptr(values)))
+
+    def find(self, queries, out=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(queries)
+        with torch.cuda.device(self.device):
+            self._stream()
+            _check(lib().ght_batch_find(self._b, _ptr(queries), _ptr(out)))
+        return out
+
+    def run(self, keys, values, queries, out=None):
+        """Build and find in one CUDA-graph launch."""
+        import torch
+        if out is None:
+            out = torch.empty_like(queries)
+        with torch.cuda.device(self.device):
+            self._stream()
+            _check(lib().ght_batch_run(self._b, _ptr(keys), _ptr(values), _ptr(queries), _ptr(out)))
+        return out
+
+    def autotune(self, keys, values, queries, out=None) -> dict:
+        import torch
+        if out is None:
+            out = torch.empty_like(queries)
+        with torch.cuda.device(self.device):
+            self._stream()
+            _check(lib().ght_batch_autotune(self._b, _ptr(keys), _ptr(values), _ptr(queries), _ptr(out)))
+        return self.stats()
+
+    def stats(self) -> dict:
+        s = GhtBatchStats()
+        _check(lib().ght_batch_stats(self._b, C.byref(s)))
+        return s.as_dict()
+
+    def table_stats(self, t: int) -> dict:
+        s = GhtStats()
+        _check(lib().ght_batch_table_stats(self._b, t, C.byref(s)))
+        return s.as_dict()
+
+    def export(self, t: int):
+        import numpy as np
+        n = self.table_stats(t)["num_slots"]
+        out = np.empty(n, dtype=np.uint64)
+        _check(lib().ght_batch_export(self._b, t, out.ctypes.data, n))
+        return out

@@ -17,55 +17,16 @@
 
 #include "ght.h"
 #include "ght_device.cuh"
+#include "ght_host.h"
 #include "ght_internal.h"
 
 namespace {
 
-thread_local std::string g_err;
+using ght::host::cuda_fail;
+using ght::host::fail;
+using ght::host::pool_alloc;
 
-int fail(int code, const char *fmt, ...) {
-  char buf[512];
-  va_list ap;
-  va_start(ap, fmt);
-  vsnprintf(buf, sizeof buf, fmt, ap);
-  va_end(ap);
-  g_err = buf;
-  return code;
-}
-
-int cuda_fail(cudaError_t e, const char *what) {
-  return fail(GHT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
-}
-
-// SplitMix64 (Steele, Lea, Flood, OOPSLA 2014), used to turn a seed into the
-// randomly generated hash constants of Sec. VII.
-uint64_t splitmix64(uint64_t &state) {
-  state += 0x9E3779B97F4A7C15ull;
-  uint64_t z = state;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
-// Wait for `ev` with a deadline instead of an unbounded synchronize.
-int wait_event(cudaEvent_t ev, double seconds) {
-  const auto t0 = std::chrono::steady_clock::now();
-  for (uint64_t spins = 0;; ++spins) {
-    const cudaError_t e = cudaEventQuery(ev);
-    if (e == cudaSuccess) return GHT_OK;
-    if (e != cudaErrorNotReady) return cuda_fail(e, "waiting for the device");
-    if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > seconds)
-      return fail(GHT_ERR_DEVICE_TIMEOUT, "device work did not finish within %.0f s", seconds);
-    if (spins > 1000) std::this_thread::sleep_for(std::chrono::microseconds(20));
-    else std::this_thread::yield();
-  }
-}
-
-double wait_limit_seconds() {
-  const char *s = getenv("GHT_WAIT_TIMEOUT_S");
-  const double v = s ? atof(s) : 0.0;
-  return v > 0.0 ? v : 300.0;
-}
+using ght::host::wait_event;
 
 constexpr uint64_t kCtrlBytes = sizeof(ght::Ctrl);
 
@@ -169,39 +130,6 @@ uint64_t bytes_of(const Shape &s) {
   return kCtrlBytes + ((slots + 255ull) & ~255ull);
 }
 
-// The library's own stream-ordered pool (one per device) for staging and
-// grouping scratch of tables whose storage the library owns. Freed blocks
-// stay cached in the pool, so repeated builds do not return to the driver.
-cudaError_t library_pool(cudaMemPool_t *out) {
-  static std::mutex mu;
-  static cudaMemPool_t pools[64] = {};
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(mu);
-  if (!pools[dev]) {
-    cudaMemPoolProps props;
-    memset(&props, 0, sizeof props);
-    props.allocType = cudaMemAllocationTypePinned;
-    props.location.type = cudaMemLocationTypeDevice;
-    props.location.id = dev;
-    e = cudaMemPoolCreate(&pools[dev], &props);
-    if (e != cudaSuccess) return e;
-    uint64_t keep = ~0ull;
-    cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
-  }
-  *out = pools[dev];
-  return cudaSuccess;
-}
-
-cudaError_t pool_alloc(void **p, uint64_t bytes, cudaStream_t s) {
-  cudaMemPool_t pool;
-  const cudaError_t e = library_pool(&pool);
-  if (e != cudaSuccess) return e;
-  return cudaMallocFromPoolAsync(p, bytes, pool, s);
-}
-
 // Grouping shape: at most 512 groups of 2^shift consecutive buckets.
 void group_shape(uint64_t m, int *shift, uint32_t *groups) {
   int bits = 0;
@@ -247,15 +175,8 @@ struct ght_table {
   mutable uint64_t insert_probes = 0, insert_retries = 0, insert_evictions = 0, longest_chain = 0;
 
   void derive(uint32_t attempt) {
-    uint64_t st = seed ^ ((uint64_t)attempt * 0x9E3779B97F4A7C15ull);
-    for (int i = 0; i < shape.h; ++i) {
-      const uint64_t x = splitmix64(st), y = splitmix64(st);
-      a[i] = (uint32_t)(1u + x % (uint64_t)(ght::kPrime - 1u));
-      c[i] = (uint32_t)(y % (uint64_t)ght::kPrime);
-    }
-    for (int i = shape.h; i < 4; ++i) a[i] = c[i] = 0;
-    uint64_t r = seed ^ 0x4B45524E454Cull ^ ((uint64_t)attempt << 32);
-    rng_seed = (uint32_t)splitmix64(r) | 1u;
+    ght::host::derive_constants(seed, attempt, shape.h, a, c);
+    rng_seed = ght::host::derive_rng_seed(seed, attempt);
   }
 
   ght::TableView view() const {
@@ -331,7 +252,7 @@ int read_ctrl(const ght_table *t) {
   if (e != cudaSuccess) return cuda_fail(e, "reading the control block");
   e = cudaEventRecord(t->done, t->stream);
   if (e != cudaSuccess) return cuda_fail(e, "recording an event");
-  return wait_event(t->done, wait_limit_seconds());
+  return wait_event(t->done);
 }
 
 // One build from device-resident keys: fill, (group,) insert, status; retry
@@ -412,7 +333,7 @@ extern "C" {
 
 const char *ght_version(void) { return "ght 0.1 (sm_103a)"; }
 
-const char *ght_last_error(void) { return g_err.c_str(); }
+const char *ght_last_error(void) { return ght::host::last_error(); }
 
 int ght_default_config(int scheme, ght_config *out) {
   if (!out) return fail(GHT_ERR_INVALID_ARG, "out is NULL");
@@ -515,8 +436,10 @@ int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_value
                                    (unsigned long long)t->capacity);
   if (n > 0 && (!h_keys || !h_values)) return fail(GHT_ERR_INVALID_ARG, "keys or values is NULL");
   if (n == 0) return build_device(t, nullptr, nullptr, 0, 0);
-  // Stage the pairs on the device (two copies on the table stream; the
-  // library pool keeps the staging block for the next call), then build.
+  // Stage the pairs on the device (the library pool keeps the block for the
+  // next call). An input-order build inserts each chunk as soon as it has
+  // landed, overlapping the copies with the inserts of the first attempt;
+  // later attempts, and grouped builds, run from the staged copy.
   void *buf = nullptr;
   const uint64_t arr = (n * sizeof(uint32_t) + 255ull) & ~255ull;
   cudaError_t e = pool_alloc(&buf, 2 * arr, t->stream);
@@ -526,14 +449,75 @@ int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_value
   }
   uint32_t *d_k = static_cast<uint32_t *>(buf), *d_v = d_k + arr / sizeof(uint32_t);
   int rc = GHT_OK;
-  if ((e = cudaMemcpyAsync(d_k, h_keys, n * 4, cudaMemcpyHostToDevice, t->stream)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(d_v, h_values, n * 4, cudaMemcpyHostToDevice, t->stream)) != cudaSuccess)
-    rc = cuda_fail(e, "staging keys");
-  if (rc == GHT_OK) rc = build_device(t, d_k, d_v, n, 0);
+  if (wants_grouping(t, n)) {
+    if ((e = cudaMemcpyAsync(d_k, h_keys, n * 4, cudaMemcpyHostToDevice, t->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d_v, h_values, n * 4, cudaMemcpyHostToDevice, t->stream)) != cudaSuccess)
+      rc = cuda_fail(e, "staging keys");
+    if (rc == GHT_OK) rc = build_device(t, d_k, d_v, n, 0);
+  } else {
+    cudaStream_t copy = nullptr;
+    cudaEvent_t landed[2] = {nullptr, nullptr};
+    if ((e = cudaStreamCreateWithFlags(&copy, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&landed[0], cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&landed[1], cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventRecord(landed[0], t->stream)) != cudaSuccess ||  // staging block allocated
+        (e = cudaStreamWaitEvent(copy, landed[0], 0)) != cudaSuccess)
+      rc = cuda_fail(e, "creating the copy pipeline");
+    if (rc == GHT_OK) {
+      t->built = false;
+      t->n_stored = 0;
+      t->derive(0);
+      const ght::TableView tv = t->view();
+      cudaEventRecord(t->tev[0], t->stream);
+      if ((e = ght::launch_fill(tv, t->shape.m * (uint64_t)t->shape.b, t->stream)) != cudaSuccess)
+        rc = cuda_fail(e, "launching fill");
+      cudaEventRecord(t->tev[1], t->stream);
+      cudaEventRecord(t->tev[2], t->stream);
+      for (uint64_t off = 0, i = 0; rc == GHT_OK && off < n; off += kChunk, ++i) {
+        const uint64_t len = std::min(kChunk, n - off);
+        cudaEvent_t ev = landed[i & 1];
+        if ((e = cudaMemcpyAsync(d_k + off, h_keys + off, len * 4, cudaMemcpyHostToDevice, copy)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(d_v + off, h_values + off, len * 4, cudaMemcpyHostToDevice, copy)) != cudaSuccess ||
+            (e = cudaEventRecord(ev, copy)) != cudaSuccess || (e = cudaStreamWaitEvent(t->stream, ev, 0)) != cudaSuccess) {
+          rc = cuda_fail(e, "staging keys");
+          break;
+        }
+        if ((e = launch_insert(t, d_k + off, d_v + off, len)) != cudaSuccess) rc = cuda_fail(e, "launching insert");
+      }
+      cudaEventRecord(t->tev[3], t->stream);
+      t->timed_build = true;
+      t->last_grouped = false;
+      if (rc == GHT_OK) rc = read_ctrl(t);
+      if (rc == GHT_OK) {
+        const uint32_t st = t->h_ctrl->status;
+        t->attempts = 1;
+        t->insert_probes = t->h_ctrl->insert_probes;
+        t->insert_retries = t->h_ctrl->insert_retries;
+        t->insert_evictions = t->h_ctrl->insert_evictions;
+        t->longest_chain = t->h_ctrl->longest_chain;
+        if (st == 0u) {
+          t->built = true;
+          t->n_stored = n;
+        } else if (st & ght::kStatusSentinel) {
+          rc = fail(GHT_ERR_SENTINEL_KEY, "an input key is the sentinel 0xFFFFFFFF");
+        } else if (st & ght::kStatusTimeout) {
+          rc = fail(GHT_ERR_DEVICE_TIMEOUT, "a key exceeded the per-key step bound");
+        } else if (st & ght::kStatusCorrupt) {
+          rc = fail(GHT_ERR_CUDA, "table corrupt: an evicted key did not hash to its bucket");
+        } else {
+          rc = build_device(t, d_k, d_v, n, 1);  // the staged copy is complete: the stream waited on it
+        }
+      }
+    }
+    if (copy) cudaStreamSynchronize(copy);
+    if (landed[0]) cudaEventDestroy(landed[0]);
+    if (landed[1]) cudaEventDestroy(landed[1]);
+    if (copy) cudaStreamDestroy(copy);
+  }
   cudaFreeAsync(buf, t->stream);
   if (rc == GHT_OK) {
     e = cudaEventRecord(t->done, t->stream);
-    rc = e == cudaSuccess ? wait_event(t->done, wait_limit_seconds()) : cuda_fail(e, "recording an event");
+    rc = e == cudaSuccess ? wait_event(t->done) : cuda_fail(e, "recording an event");
   }
   return rc;
 }
@@ -593,7 +577,7 @@ int ght_find_host(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out
   cudaFreeAsync(d_buf, t->stream);
   if (rc == GHT_OK) {
     e = cudaEventRecord(t->done, t->stream);
-    rc = e == cudaSuccess ? wait_event(t->done, wait_limit_seconds()) : cuda_fail(e, "recording an event");
+    rc = e == cudaSuccess ? wait_event(t->done) : cuda_fail(e, "recording an event");
   } else {
     cudaStreamSynchronize(up);
     cudaStreamSynchronize(down);
@@ -686,7 +670,7 @@ int ght_export(const ght_table *t, uint64_t *h_slots, uint64_t n_slots) {
   if (e != cudaSuccess) return cuda_fail(e, "exporting slots");
   e = cudaEventRecord(t->done, t->stream);
   if (e != cudaSuccess) return cuda_fail(e, "recording an event");
-  return wait_event(t->done, wait_limit_seconds());
+  return wait_event(t->done);
 }
 
 int ght_hash_device(const ght_table *t, const uint32_t *d_keys, uint32_t *d_buckets, uint64_t n) {
@@ -773,5 +757,5 @@ extern "C" int ght_find_host_noalloc(const ght_table *t, const uint32_t *h_queri
   if (e != cudaSuccess) return cuda_fail(e, "copying results back");
   e = cudaEventRecord(t->done, t->stream);
   if (e != cudaSuccess) return cuda_fail(e, "recording an event");
-  return wait_event(t->done, wait_limit_seconds());
+  return wait_event(t->done);
 }

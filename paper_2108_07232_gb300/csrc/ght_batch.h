@@ -1,0 +1,35 @@
+// ght_batch.h -- device-side view of a batch of BCHT tables (kern_batch.cu).
+#pragma once
+
+#include "ght_internal.h"
+
+namespace ght {
+
+// Descriptor of one table of a batch (64 bytes, device memory).
+struct BatchTable {
+  uint64_t *slots;  // m * 16 pairs
+  FastMod mod;      // remainder by m
+  uint32_t a[4], c[4];
+  uint32_t status;  // build status bits of this table
+  uint32_t m;
+};
+static_assert(sizeof(BatchTable) == 64, "batch descriptor is 64 bytes");
+
+struct BatchView {
+  BatchTable *tables;
+  const uint64_t *key_offs;    // num_tables + 1 prefix offsets into the key/value arrays
+  const uint64_t *query_offs;  // num_tables + 1 prefix offsets into the query/result arrays
+  Ctrl *ctrl;                  // batch-wide probe counters
+  uint32_t t_lo, t_hi;         // tables this launch covers
+  int32_t h;
+  uint32_t max_chain, max_steps, rng_seed;
+};
+
+bool batch_shape_supported(int tile_lanes, int keys_per_lane);
+cudaError_t launch_batch_fill(const BatchView &bv, uint64_t *slots, uint64_t num_slots, cudaStream_t s);
+cudaError_t launch_batch_insert(const BatchView &bv, const uint32_t *k, const uint32_t *v, uint64_t items,
+                                const LaunchOpts &o, cudaStream_t s);
+cudaError_t launch_batch_find(const BatchView &bv, const uint32_t *q, uint32_t *out, uint64_t items,
+                              const LaunchOpts &o, cudaStream_t s);
+
+}  // namespace ght

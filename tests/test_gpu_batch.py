@@ -1,0 +1,118 @@
+"""Batched tables (many BCHT tables per launch) against the oracle, through the
+C ABI: every table's finds equal the definitional lookup over that table's own
+pairs, every table's layout passes the oracle validator, and the graph path,
+the plain batched path and the autotuned shapes agree."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_07232_gb300 import build
+    build.build()
+    import paper_2108_07232_gb300 as G
+    return G
+
+
+@pytest.fixture(scope="module")
+def work():
+    # uneven sizes from 2^4 (below one warp) to 2^14, load factors 0.8..0.99
+    return W.make_batch(41, 4, 14, 0.8, 0.99, 2.0, 0.5, seed=21)
+
+
+def _check_tables(G, batch, work, out, validate=True):
+    keys, vals, q = work["keys"], work["values"], work["queries"]
+    ko, qo = work["key_offsets"], work["query_offsets"]
+    got = O._u32(out.cpu())
+    for t in range(batch.num_tables):
+        k, v = keys[ko[t]:ko[t + 1]], vals[ko[t]:ko[t + 1]]
+        qq = q[qo[t]:qo[t + 1]]
+        assert (got[qo[t]:qo[t + 1]] == O.lookup(k, v, qq)).all(), t
+        if validate:
+            st = batch.table_stats(t)
+            assert st["built"] == 1 and st["n_stored"] == k.numel()
+            T = O.Table(O.BCHT, int(work["capacities"][t]), float(work["load_factors"][t]), m=st["num_buckets"])
+            T.set_constants(st["hash_a"], st["hash_c"])
+            ok, msg = T.validate(k, v, slots=batch.export(t))
+            assert ok, (t, msg)
+
+
+def test_batch_graph_run_parity(G, work):
+    b = G.Batch(work["capacities"], work["load_factors"], seed=3)
+    b.set_layout(work["key_offsets"], work["query_offsets"])
+    k, v, q = work["keys"].cuda(), work["values"].cuda(), work["queries"].cuda()
+    out = b.run(k, v, q)
+    st = b.stats()
+    assert st["graph_launches"] == 1 and st["tables_failed"] == 0
+    _check_tables(G, b, work, out)
+    # a second run replays the same graph; results identical
+    out2 = b.run(k, v, q)
+    assert b.stats()["graph_launches"] == 2
+    assert torch.equal(out, out2)
+    # constants per table follow the single-table derivation from seed + t * phi
+    st0 = b.table_stats(5)
+    a, c = O.derive_constants((3 + 5 * 0x9E3779B97F4A7C15) % 2**64, st0["attempts"] - 1, 3)
+    assert st0["hash_a"] == a and st0["hash_c"] == c
+
+
+def test_batch_plain_and_autotuned_paths_agree(G, work):
+    b = G.Batch(work["capacities"], work["load_factors"], seed=4, build_tile_lanes=8, keys_per_lane=1)
+    b.set_layout(work["key_offsets"], work["query_offsets"])
+    k, v, q = work["keys"].cuda(), work["values"].cuda(), work["queries"].cuda()
+    b.build(k, v)
+    out = b.find(q)
+    _check_tables(G, b, work, out)
+    tuned = b.autotune(k, v, q)
+    assert tuned["tuned"] == 1
+    out2 = b.run(k, v, q)
+    _check_tables(G, b, work, out2, validate=False)
+
+
+def test_batch_edge_cases(G):
+    caps = np.array([0, 5, 100, 3000], dtype=np.uint64)
+    lfs = np.array([0.5, 0.9, 0.95, 0.99])
+    keys = W.make_keys(3105, 9)
+    vals = W.make_values(3105, 9)
+    ko = np.array([0, 0, 5, 105, 3105], dtype=np.uint64)
+    q = torch.cat([keys[:50], W.make_negatives(3105, 30, 9)])
+    qo = np.array([0, 10, 10, 40, 80], dtype=np.uint64)  # table 1 has no queries
+    b = G.Batch(caps, lfs, seed=1)
+    b.set_layout(ko, qo)
+    out = O._u32(b.run(keys.cuda(), vals.cuda(), q.cuda()).cpu())
+    for t in range(4):
+        assert (out[qo[t]:qo[t + 1]] == O.lookup(keys[ko[t]:ko[t + 1]], vals[ko[t]:ko[t + 1]],
+                                                  q[qo[t]:qo[t + 1]])).all()
+    # too many keys for a table's capacity
+    with pytest.raises(G.GhtError) as e:
+        b.set_layout(np.array([0, 1, 5, 105, 3106], dtype=np.uint64), qo)
+    assert e.value.status == "GHT_ERR_CAPACITY"
+    # sentinel key in one table
+    bad = keys.clone()
+    bad[200] = -1
+    with pytest.raises(G.GhtError) as e:
+        b.build(bad.cuda(), vals.cuda())
+    assert e.value.status == "GHT_ERR_SENTINEL_KEY"
+
+
+def test_batch_reports_tables_that_never_build(G):
+    """A chain bound of one exchange cannot build tables at LF 0.99: every
+    attempt of those tables fails and the batch reports them."""
+    work = W.make_batch(6, 12, 13, 0.99, 0.99, 1.0, 1.0, seed=5)
+    b = G.Batch(work["capacities"], work["load_factors"], seed=1, max_chain=1, max_attempts=3)
+    b.set_layout(work["key_offsets"], work["query_offsets"])
+    with pytest.raises(G.GhtError) as e:
+        b.build(work["keys"].cuda(), work["values"].cuda())
+    assert e.value.status == "GHT_ERR_BUILD_FAILED"
+    st = b.stats()
+    assert st["tables_failed"] > 0 and st["rebuilds"] >= 2 * st["tables_failed"]
+    with pytest.raises(G.GhtError):
+        b.find(work["queries"].cuda())

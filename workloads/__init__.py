@@ -151,3 +151,41 @@ def make_workload(n: int, n_queries: int, positive_fraction: float, seed: int,
     negs = make_negatives(n, n_neg, seed, device) if n_neg else None
     q = make_queries(keys, n_queries, positive_fraction, seed, negs)
     return keys, vals, q
+
+
+def uniform01(index: int, seed: int) -> float:
+    """Counter-based uniform draw in [0, 1) (53-bit), for per-table parameters."""
+    z = _splitmix64_stream(seed ^ (index * 0x9E3779B97F4A7C15), 1)[0]
+    return (z >> 11) / float(1 << 53)
+
+
+def make_batch(num_tables: int, log2_min: int, log2_max: int, lf_lo: float, lf_hi: float,
+               queries_per_key: float, positive_fraction: float, seed: int, device="cpu"):
+    """Independent tables with key counts floor(2^(log2_min + (log2_max-log2_min) u)),
+    u ~ U[0, 1), load factors ~ U[lf_lo, lf_hi], and round(queries_per_key * n)
+    queries per table at the given positive fraction. Returns a dict with the
+    per-table capacities and load factors, the concatenated keys, values and
+    queries (int32 bits) and the (num_tables + 1) key and query offsets."""
+    import numpy as np
+
+    sizes, lfs = [], []
+    for t in range(num_tables):
+        u = uniform01(t, seed ^ 0x73697A65)
+        sizes.append(int(2.0 ** (log2_min + (log2_max - log2_min) * u)))
+        lfs.append(lf_lo + (lf_hi - lf_lo) * uniform01(t, seed ^ 0x6C66))
+    keys, vals, qs = [], [], []
+    for t, n in enumerate(sizes):
+        k, v, q = make_workload(n, int(round(queries_per_key * n)), positive_fraction, seed + 7919 * (t + 1),
+                                device)
+        keys.append(k)
+        vals.append(v)
+        qs.append(q)
+    key_offs = np.zeros(num_tables + 1, dtype=np.uint64)
+    key_offs[1:] = np.cumsum(sizes)
+    q_offs = np.zeros(num_tables + 1, dtype=np.uint64)
+    q_offs[1:] = np.cumsum([q.numel() for q in qs])
+    return {
+        "capacities": np.array(sizes, dtype=np.uint64), "load_factors": np.array(lfs, dtype=np.float64),
+        "keys": torch.cat(keys), "values": torch.cat(vals), "queries": torch.cat(qs),
+        "key_offsets": key_offs, "query_offsets": q_offs,
+    }
