@@ -43,8 +43,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile-lanes", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
-    ap.add_argument("--workload", choices=["hbm", "batched"], default="hbm",
-                    help="hbm: 2^28-key BCHT tables (default); batched: 512 uneven tables in one graph launch")
+    ap.add_argument("--workload", choices=["hbm", "batched", "served"], default="hbm",
+                    help="hbm: 2^28-key BCHT tables (default); batched: 512 uneven tables in one graph "
+                         "launch; served: a table pool under Poisson request arrivals")
+    ap.add_argument("--served-seconds", type=float, default=1.0, help="served: length of the arrival trace")
     return ap.parse_args()
 
 
@@ -453,6 +455,97 @@ def run_batched(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_served(args, world, rank, local):
+    """128 resident BCHT tables of 2^16..2^24 keys (log-uniform) at LF 0.95 in a
+    pool with a 60 GB budget. A Poisson stream of find batches (sizes
+    log-uniform in [1, 2^20], 70 % positive keys) at 80 % of the pool's
+    measured capacity, plus a build request of a new 2^20..2^24-key table every
+    100 ms, is replayed through the pool (continuous batching) and as serial
+    plain calls; p50/p99 latency and aggregate throughput of both."""
+    import numpy as np
+    import torch
+
+    import paper_2108_07232_gb300 as G
+    import workloads as W
+    from paper_2108_07232_gb300 import build as B
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+    seed = SEED + 2 + rank
+    rng = np.random.default_rng(seed)
+    pool = G.Pool(60 << 30, device=dev)
+    sizes = [int(2 ** (16 + 8 * W.uniform01(t, seed))) for t in range(128)]
+    qpool, ids = [], []
+    for t, n in enumerate(sizes):
+        k, v = W.make_keys(n, seed + t, device=dev), W.make_values(n, seed + t, device=dev)
+        tk, tid = pool.submit_build(n, 0.95, seed + t, k, v)
+        pool.wait(tk, timeout=600)
+        ids.append(tid)
+        qpool.append(W.make_queries(k, 1 << 20, 0.7, seed + 1000 + t))
+        del k, v
+
+    def make_trace(count, rate):
+        arr = np.cumsum(rng.exponential(1.0 / rate, count)) if rate else np.zeros(count)
+        tr = []
+        for i in range(count):
+            t = int(rng.integers(0, 128))
+            size = int(2 ** rng.uniform(0, 20))
+            off = int(rng.integers(0, (1 << 20) - size + 1))
+            q = qpool[t][off:off + size]
+            tr.append({"kind": "find", "table": ids[t], "queries": q, "out": torch.empty_like(q),
+                       "arrival_s": float(arr[i])})
+        return tr
+
+    # capacity: a burst of requests all arriving at once
+    burst = make_trace(2000, 0)
+    pool.replay(burst)
+    _, _, mk = pool.replay(burst)
+    burst_q = sum(t["queries"].numel() for t in burst)
+    capacity_qps = burst_q / mk
+    mean_size = burst_q / len(burst)
+    rate = 0.8 * capacity_qps / mean_size
+    count = max(100, int(rate * args.served_seconds))
+    trace = make_trace(count, rate)
+    span = trace[-1]["arrival_s"]
+    n_builds = int(span / 0.1)
+    builds = []
+    for j in range(n_builds):
+        n = int(2 ** (20 + 4 * W.uniform01(j, seed ^ 0x62)))
+        k, v = W.make_keys(n, seed + 5000 + j, device=dev), W.make_values(n, seed + 5000 + j, device=dev)
+        builds.append({"kind": "build", "keys": k, "values": v, "capacity": n, "load_factor": 0.95,
+                       "seed": seed + 5000 + j, "arrival_s": 0.1 * (j + 1)})
+    full = sorted(trace + builds, key=lambda r: r["arrival_s"])
+    out = {}
+    for mode in ("pool", "serial"):
+        for r in full:
+            if r["kind"] == "find":
+                r["out"] = torch.empty_like(r["queries"])
+        lat, st, mk = pool.replay(full, serial=(mode == "serial"))
+        fl = np.array([lat[i] for i, r in enumerate(full) if r["kind"] == "find"])
+        keys_done = sum(r["queries"].numel() if r["kind"] == "find" else r["keys"].numel() for r in full)
+        out[mode] = {"p50_ms": round(1e3 * float(np.percentile(fl, 50)), 3),
+                     "p99_ms": round(1e3 * float(np.percentile(fl, 99)), 3),
+                     "gkeys_s": round(keys_done / mk / 1e9, 3), "makespan_s": round(mk, 4),
+                     "ok": bool((st == 0).all()),
+                     "outs": [r["out"] for r in full if r["kind"] == "find"]}
+    same = all(torch.equal(a, b) for a, b in zip(out["pool"].pop("outs"), out["serial"].pop("outs")))
+    st = pool.stats()
+    line = {
+        "metric": "served p50/p99 find latency and Gkeys/s, 128 resident BCHT tables, continuous batching",
+        "value": out["pool"]["p99_ms"], "unit": "ms (p99 find latency)", "n_gpus": 1, "steps": 1, "warmup": 1,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "served_128_bcht_n2^16..2^24_lf0.95_budget60GB", "find_requests": count,
+                   "build_requests": n_builds, "arrival_rate_per_s": round(rate, 1),
+                   "offered_load": "0.8 x measured capacity", "mean_find_size": round(mean_size, 1),
+                   "input_seed": seed},
+        "capacity_gqueries_s": round(capacity_qps / 1e9, 3), "pool": out["pool"], "serial_plain_calls": out["serial"],
+        "results_identical": same, "mean_requests_per_launch": round(st["mean_requests_per_launch"], 2),
+    }
+    pool.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -461,6 +554,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args, world, rank, local)
+        return
+    if args.workload == "served":
+        run_served(args, world, rank, local)
         return
     run_ours(args, world, rank, local)
 

@@ -296,6 +296,90 @@ int ght_batch_export(const ght_batch *b, uint32_t table, uint64_t *h_slots, uint
 
 void ght_batch_destroy(ght_batch *b);
 
+/* ---------------------------------------------------------------------------
+ * Served pool: device-resident BCHT tables answering a stream of find
+ * requests and admitting build requests under an HBM budget. Not in the
+ * paper: it serves the paper's tables to many clients.
+ *
+ * Continuous batching: a scheduler thread keeps up to two batched find
+ * launches in flight; each new launch takes every pending find whose table is
+ * built (oldest first, at most 2^22 queries and 4096 requests), gathers their
+ * queries, finds them in one launch and scatters the answers, so requests that
+ * arrive while others run join the next launch. A build worker admits build
+ * requests in arrival order once the table fits in the budget (storage from
+ * the library's stream-ordered pool) and builds on its own stream, overlapping
+ * the finds. Each answer is exactly what a single-table find returns.
+ * Device arrays passed to submit calls must stay valid until the request
+ * completes.
+ * ------------------------------------------------------------------------- */
+typedef struct ght_pool ght_pool; /* opaque, library-owned */
+
+typedef struct {
+  int32_t status;           /* ght_status of the request */
+  int32_t kind;             /* 0 find, 1 build */
+  uint32_t table;
+  int32_t launch_requests;  /* find requests packed into the same launch */
+  uint64_t n;
+  double queue_s;           /* submit -> start of its launch (or build) */
+  double latency_s;         /* submit (or scheduled arrival) -> completion */
+} ght_pool_result_t;
+
+typedef struct {
+  uint64_t budget_bytes, used_bytes;
+  uint32_t tables, tables_ready;
+  uint64_t find_launches, finds_done, queries_done, builds_done, builds_refused;
+  uint64_t pending_finds, pending_builds;
+  double mean_requests_per_launch;
+} ght_pool_stats_t;
+
+/* One request of a replayed trace. */
+typedef struct {
+  int32_t kind;             /* 0 find, 1 build */
+  uint32_t table;           /* find: table id */
+  const uint32_t *d_in;     /* find: queries; build: keys */
+  const uint32_t *d_values; /* build: values */
+  uint32_t *d_out;          /* find: answers */
+  uint64_t n;               /* queries or pairs */
+  uint64_t capacity;        /* build */
+  double load_factor;       /* build */
+  uint64_t seed;            /* build */
+  double arrival_s;         /* arrival time from the start of the replay */
+} ght_pool_request_t;
+
+/* Create a pool on the current device with `hbm_budget_bytes` for table
+ * storage; cfg (may be NULL) supplies max_chain, max_attempts and shapes. */
+ght_pool *ght_pool_create(uint64_t hbm_budget_bytes, const ght_config *cfg);
+
+/* Queue a build of a new table (capacity, load factor, seed) from n pairs;
+ * *table_id receives the new table's id at once (finds on it wait for the
+ * build). Returns a ticket, 0 on invalid arguments. A table larger than the
+ * whole budget completes with GHT_ERR_OOM. */
+uint64_t ght_pool_submit_build(ght_pool *p, uint64_t capacity, double load_factor, uint64_t seed,
+                               const uint32_t *d_keys, const uint32_t *d_values, uint64_t n, uint32_t *table_id);
+
+/* Queue a find of n queries on a table; returns a ticket (0 on error). */
+uint64_t ght_pool_submit_find(ght_pool *p, uint32_t table_id, const uint32_t *d_queries, uint32_t *d_out, uint64_t n);
+
+/* Wait (at most timeout_s) for a request; fills *out (may be NULL) and
+ * forgets the ticket. Returns the request's status. */
+int ght_pool_wait(ght_pool *p, uint64_t ticket, double timeout_s, ght_pool_result_t *out);
+
+/* Drop a built table; its storage returns to the budget once no launch reads it. */
+int ght_pool_drop_table(ght_pool *p, uint32_t table_id);
+
+int ght_pool_stats(ght_pool *p, ght_pool_stats_t *out);
+
+/* Replay `count` requests at their arrival times: through the pool
+ * (serial = 0) or as plain single-table calls one at a time in arrival order
+ * (serial = 1). latency_s[i] = completion - scheduled arrival; status[i];
+ * *makespan_s = last completion - start. Arrays may be NULL. */
+int ght_pool_replay(ght_pool *p, const ght_pool_request_t *trace, uint64_t count, int serial, double *latency_s,
+                    int32_t *status, double *makespan_s);
+
+/* Stop the scheduler threads (after the queued requests finish) and free
+ * everything. */
+void ght_pool_destroy(ght_pool *p);
+
 #ifdef __cplusplus
 }
 #endif

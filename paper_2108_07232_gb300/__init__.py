@@ -14,7 +14,7 @@ from __future__ import annotations
 
 from ._binding import (  # noqa: F401
     BCHT, BCHT_LB, CUCKOO1, EMPTY, IHT, P2BHT, SCHEMES, Batch, GhtBatchStats, GhtConfig, GhtError, GhtStats,
-    HashTable,
+    HashTable, Pool,
     ght_build, ght_build_host, ght_create, ght_create_ex, ght_default_config, ght_destroy,
     ght_export, ght_find, ght_find_host, ght_find_host_noalloc, ght_hash_device, ght_hash_host, ght_last_error,
     ght_reset_counters, ght_set_stream, ght_stats, ght_table_bytes, ght_version, lib, lib_path,
@@ -22,6 +22,6 @@ from ._binding import (  # noqa: F401
 )
 
 __all__ = [
-    "BCHT", "P2BHT", "IHT", "CUCKOO1", "BCHT_LB", "EMPTY", "SCHEMES", "HashTable", "Batch", "GhtError",
+    "BCHT", "P2BHT", "IHT", "CUCKOO1", "BCHT_LB", "EMPTY", "SCHEMES", "HashTable", "Batch", "Pool", "GhtError",
     "GhtConfig", "GhtStats", "lib", "lib_path",
 ]

@@ -74,6 +74,36 @@ class GhtBatchStats(C.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class GhtPoolResult(C.Structure):
+    _fields_ = [
+        ("status", C.c_int32), ("kind", C.c_int32), ("table", C.c_uint32), ("launch_requests", C.c_int32),
+        ("n", C.c_uint64), ("queue_s", C.c_double), ("latency_s", C.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class GhtPoolStats(C.Structure):
+    _fields_ = [
+        ("budget_bytes", C.c_uint64), ("used_bytes", C.c_uint64), ("tables", C.c_uint32),
+        ("tables_ready", C.c_uint32), ("find_launches", C.c_uint64), ("finds_done", C.c_uint64),
+        ("queries_done", C.c_uint64), ("builds_done", C.c_uint64), ("builds_refused", C.c_uint64),
+        ("pending_finds", C.c_uint64), ("pending_builds", C.c_uint64), ("mean_requests_per_launch", C.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class GhtPoolRequest(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int32), ("table", C.c_uint32), ("d_in", C.c_void_p), ("d_values", C.c_void_p),
+        ("d_out", C.c_void_p), ("n", C.c_uint64), ("capacity", C.c_uint64), ("load_factor", C.c_double),
+        ("seed", C.c_uint64), ("arrival_s", C.c_double),
+    ]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -124,6 +154,14 @@ def lib():
                 "ght_batch_table_stats": ([vp, C.c_uint32, C.POINTER(GhtStats)], i32),
                 "ght_batch_export": ([vp, C.c_uint32, vp, u64], i32),
                 "ght_batch_destroy": ([vp], None),
+                "ght_pool_create": ([u64, C.POINTER(GhtConfig)], vp),
+                "ght_pool_submit_build": ([vp, u64, C.c_double, u64, vp, vp, u64, C.POINTER(C.c_uint32)], u64),
+                "ght_pool_submit_find": ([vp, C.c_uint32, vp, vp, u64], u64),
+                "ght_pool_wait": ([vp, u64, C.c_double, C.POINTER(GhtPoolResult)], i32),
+                "ght_pool_drop_table": ([vp, C.c_uint32], i32),
+                "ght_pool_stats": ([vp, C.POINTER(GhtPoolStats)], i32),
+                "ght_pool_replay": ([vp, vp, u64, i32, vp, vp, C.POINTER(C.c_double)], i32),
+                "ght_pool_destroy": ([vp], None),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -497,3 +535,98 @@ class Batch:
         out = np.empty(n, dtype=np.uint64)
         _check(lib().ght_batch_export(self._b, t, out.ctypes.data, n))
         return out
+
+
+# --- served pool -----------------------------------------------------------------
+
+class Pool:
+    """Device-resident BCHT tables under an HBM budget, serving find and build
+    requests with continuous batching (see include/ght.h). Tensors passed to
+    submit calls are kept alive until their request is waited on."""
+
+    def __init__(self, budget_bytes: int, device=None, **config):
+        import torch
+
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        cfg = _config(config) if config else None
+        with torch.cuda.device(self.device):
+            p = lib().ght_pool_create(int(budget_bytes), C.byref(cfg) if cfg else None)
+        if not p:
+            raise GhtError(1, ght_last_error())
+        self._p = p
+        self._keep = {}
+
+    def close(self) -> None:
+        if getattr(self, "_p", None):
+            lib().ght_pool_destroy(self._p)
+            self._p = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit_build(self, capacity: int, load_factor: float, seed: int, keys, values):
+        tid = C.c_uint32(0)
+        tk = lib().ght_pool_submit_build(self._p, int(capacity), float(load_factor), int(seed), _ptr(keys),
+                                         _ptr(values), keys.numel(), C.byref(tid))
+        if not tk:
+            raise GhtError(1, ght_last_error())
+        self._keep[tk] = (keys, values)
+        return tk, tid.value
+
+    def submit_find(self, table: int, queries, out):
+        tk = lib().ght_pool_submit_find(self._p, int(table), _ptr(queries), _ptr(out), queries.numel())
+        if not tk:
+            raise GhtError(1, ght_last_error())
+        self._keep[tk] = (queries, out)
+        return tk
+
+    def wait(self, ticket: int, timeout: float = 60.0) -> dict:
+        r = GhtPoolResult()
+        rc = lib().ght_pool_wait(self._p, int(ticket), float(timeout), C.byref(r))
+        self._keep.pop(ticket, None)
+        if rc != 0:
+            raise GhtError(rc, ght_last_error())
+        return r.as_dict()
+
+    def drop(self, table: int) -> None:
+        _check(lib().ght_pool_drop_table(self._p, int(table)))
+
+    def stats(self) -> dict:
+        s = GhtPoolStats()
+        rc = lib().ght_pool_stats(self._p, C.byref(s))
+        if rc != 0:
+            raise GhtError(rc, ght_last_error())
+        return s.as_dict()
+
+    def replay(self, trace, serial: bool = False):
+        """trace: list of dicts with kind ('find'|'build'), table, queries/keys,
+        values, out, capacity, load_factor, seed, arrival_s. Returns
+        (latencies [s] as numpy, statuses, makespan [s])."""
+        import numpy as np
+        n = len(trace)
+        arr = (GhtPoolRequest * max(n, 1))()
+        for i, t in enumerate(trace):
+            r = arr[i]
+            build = t["kind"] == "build"
+            r.kind = 1 if build else 0
+            r.table = int(t.get("table", 0))
+            r.d_in = _ptr(t["keys"] if build else t["queries"])
+            r.d_values = _ptr(t["values"]) if build else None
+            r.d_out = None if build else _ptr(t["out"])
+            r.n = (t["keys"] if build else t["queries"]).numel()
+            r.capacity = int(t.get("capacity", 0))
+            r.load_factor = float(t.get("load_factor", 0.0))
+            r.seed = int(t.get("seed", 0))
+            r.arrival_s = float(t["arrival_s"])
+        lat = np.zeros(n, dtype=np.float64)
+        st = np.zeros(n, dtype=np.int32)
+        mk = C.c_double(0.0)
+        rc = lib().ght_pool_replay(self._p, C.addressof(arr), n, 1 if serial else 0, lat.ctypes.data, st.ctypes.data,
+                                   C.byref(mk))
+        if rc != 0:
+            raise GhtError(rc, ght_last_error())
+        return lat, st, mk.value

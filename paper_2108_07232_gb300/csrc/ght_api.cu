@@ -17,6 +17,7 @@
 
 #include "ght.h"
 #include "ght_device.cuh"
+#include "ght_batch.h"
 #include "ght_host.h"
 #include "ght_internal.h"
 
@@ -328,6 +329,19 @@ int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n,
 constexpr uint64_t kChunk = 1ull << 23;  // keys per host<->device pipeline chunk
 
 }  // namespace
+
+bool ght::table_descriptor(const ght_table *t, ght::BatchTable *out) {
+  if (!t || !t->built || t->shape.scheme != GHT_BCHT || t->shape.b != 16 || t->shape.h != 3) return false;
+  memset(out, 0, sizeof *out);
+  out->slots = t->slots;
+  out->m = (uint32_t)t->shape.m;
+  out->mod = ght::make_fastmod(out->m);
+  for (int i = 0; i < 4; ++i) {
+    out->a[i] = t->a[i];
+    out->c[i] = t->c[i];
+  }
+  return true;
+}
 
 extern "C" {
 

@@ -1,6 +1,7 @@
 // ght_batch.h -- device-side view of a batch of BCHT tables (kern_batch.cu).
 #pragma once
 
+#include "ght.h"
 #include "ght_internal.h"
 
 namespace ght {
@@ -26,6 +27,17 @@ struct BatchView {
 };
 
 bool batch_shape_supported(int tile_lanes, int keys_per_lane);
+
+// Describe a built single BCHT table (b = 16) as a batch descriptor (ght_api.cu).
+// Returns false if the table is not a built 16-pair BCHT table.
+bool table_descriptor(const struct ::ght_table *t, BatchTable *out);
+
+// Copy n items from per-segment sources into one array and back
+// (kern_batch.cu): dst[i] = src[s][i - offs[s]] for offs[s] <= i < offs[s+1].
+cudaError_t launch_segment_gather(const uint32_t *const *src, const uint64_t *offs, uint32_t segs, uint32_t *dst,
+                                  uint64_t n, cudaStream_t s);
+cudaError_t launch_segment_scatter(const uint32_t *src, uint32_t *const *dst, const uint64_t *offs, uint32_t segs,
+                                   uint64_t n, cudaStream_t s);
 cudaError_t launch_batch_fill(const BatchView &bv, uint64_t *slots, uint64_t num_slots, cudaStream_t s);
 cudaError_t launch_batch_insert(const BatchView &bv, const uint32_t *k, const uint32_t *v, uint64_t items,
                                 const LaunchOpts &o, cudaStream_t s);

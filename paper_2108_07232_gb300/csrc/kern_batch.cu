@@ -425,6 +425,56 @@ static cudaError_t find_cfg(const BatchView &bv, const uint32_t *q, uint32_t *ou
   return cudaGetLastError();
 }
 
+__device__ __forceinline__ uint32_t segment_of(const uint64_t *__restrict__ offs, uint32_t segs, uint64_t i) {
+  uint32_t lo = 0, hi = segs;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(offs + mid) <= i) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256)
+segment_gather_kernel(const uint32_t *const *__restrict__ src, const uint64_t *__restrict__ offs, uint32_t segs,
+                      uint32_t *__restrict__ dst, uint64_t n) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint32_t sg = segment_of(offs, segs, i);
+    dst[i] = __ldg(src[sg] + (i - __ldg(offs + sg)));
+  }
+}
+
+__global__ void __launch_bounds__(256)
+segment_scatter_kernel(const uint32_t *__restrict__ src, uint32_t *const *__restrict__ dst,
+                       const uint64_t *__restrict__ offs, uint32_t segs, uint64_t n) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint32_t sg = segment_of(offs, segs, i);
+    dst[sg][i - __ldg(offs + sg)] = src[i];
+  }
+}
+
+cudaError_t launch_segment_gather(const uint32_t *const *src, const uint64_t *offs, uint32_t segs, uint32_t *dst,
+                                  uint64_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  int blocks = 0;
+  cudaError_t e = grid_for(segment_gather_kernel, n, 0, &blocks);
+  if (e != cudaSuccess) return e;
+  segment_gather_kernel<<<blocks, kThreads, 0, s>>>(src, offs, segs, dst, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_segment_scatter(const uint32_t *src, uint32_t *const *dst, const uint64_t *offs, uint32_t segs,
+                                   uint64_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  int blocks = 0;
+  cudaError_t e = grid_for(segment_scatter_kernel, n, 0, &blocks);
+  if (e != cudaSuccess) return e;
+  segment_scatter_kernel<<<blocks, kThreads, 0, s>>>(src, dst, offs, segs, n);
+  return cudaGetLastError();
+}
+
 bool batch_shape_supported(int G, int kpl) {
   return (G == 4 || G == 8 || G == 16) && (kpl == 1 || kpl == 2);
 }
