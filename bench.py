@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile-lanes", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
-    ap.add_argument("--workload", choices=["hbm", "batched", "served"], default="hbm",
+    ap.add_argument("--workload", choices=["hbm", "batched", "served", "sweep", "success"], default="hbm",
                     help="hbm: 2^28-key BCHT tables (default); batched: 512 uneven tables in one graph "
                          "launch; served: a table pool under Poisson request arrivals")
     ap.add_argument("--served-seconds", type=float, default=1.0, help="served: length of the arrival trace")
@@ -55,6 +55,27 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def rank_seed(base: int, rank: int) -> int:
+    """Input seed of a rank: every rank builds and queries its own tables."""
+    return base + rank
+
+
+def reduce_max(x: float, world: int, device=None) -> float:
+    """Max of a per-rank value over all ranks (identity on one rank)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(keys_per_rank_step: int, steps: int, world: int, max_ms: float) -> float:
+    """Gkeys/s of the whole job: every rank's keys over the slowest rank's time."""
+    return world * keys_per_rank_step * steps / (max_ms / 1e3) / 1e9
 
 
 def peaks():
@@ -209,7 +230,7 @@ def run_ours(args, world, rank, local):
     if world > 1:
         dist.barrier()
     n = 1 << args.log2n
-    seed = SEED + rank
+    seed = rank_seed(SEED, rank)
     keys = W.make_keys(n, seed, device=dev)
     vals = W.make_values(n, seed, device=dev)
     pos = W.make_queries(keys, n, 1.0, seed)
@@ -272,13 +293,9 @@ def run_ours(args, world, rank, local):
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = reduce_max(ev0.elapsed_time(ev1), world, dev)
     keys_per_step = len(LFS) * 3 * n
-    value = world * keys_per_step * args.steps / (ms / 1e3) / 1e9
+    value = whole_job_value(keys_per_step, args.steps, world, ms)
     gpu_launches = launches[0]
 
     # probe counts for the algorithmic bytes: one extra counted build/find (untimed)
@@ -351,12 +368,8 @@ def run_ours(args, world, rank, local):
         for _ in range(args.steps):
             host_step()
         torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        if world > 1:
-            tt = torch.tensor([el], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            el = float(tt.item())
-        e2e = {"value": world * keys_per_step * args.steps / el / 1e9, "unit": "Gkeys/s",
+        el = reduce_max(time.perf_counter() - t0, world, dev)
+        e2e = {"value": whole_job_value(keys_per_step, args.steps, world, 1e3 * el), "unit": "Gkeys/s",
                "h2d_bytes_per_step": len(LFS) * (8 * n + 8 * n),
                "d2h_bytes_per_step": len(LFS) * 8 * n,
                "api": "HashTable.build/find on pinned CPU tensors (ght_build_host / ght_find_host)"}
@@ -546,6 +559,128 @@ def run_served(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+PAPER_PROBES = {  # (scheme, lf): (insert, find_pos, find_neg) printed in Sec. VII (50M keys, TITAN V)
+    ("bcht", 0.9): (1.11, None, None), ("bcht", 0.99): (1.43, 1.38, 2.80),
+    ("p2bht", 0.8): (2.0, 1.33, 2.0), ("iht", 0.86): (1.49, 1.33, 3.0),
+}
+
+
+def _time_ms(fn, reps=5):
+    import torch
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def run_sweep(args, world, rank, local):
+    """Config 1 (BCHT, 2^20 keys, LF 0.9, 2^20 queries at 50 % positive: the
+    table is L2-resident) and config 2 (2^24 keys; BCHT, P2BHT, IHT, 1CHT with
+    3 and 4 hash functions; LF 0.6..0.99; positive fraction 0, 0.5, 1): build and
+    find throughput per combination, probes per key, and build failures where a
+    scheme cannot reach the load factor (expected, Sec. VII-A)."""
+    import torch
+
+    import paper_2108_07232_gb300 as G
+    import workloads as W
+    from paper_2108_07232_gb300 import build as B
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+    rows = []
+
+    def measure(scheme, n, lf, fracs, seed, **cfg):
+        keys, vals = W.make_keys(n, seed, device=dev), W.make_values(n, seed, device=dev)
+        negs = W.make_negatives(n, n, seed, device=dev)
+        qs = {f: W.make_queries(keys, n, f, seed, negs) for f in fracs}
+        out = torch.empty_like(keys)
+        t = G.HashTable(scheme, n, lf, seed=seed, max_attempts=3, **cfg)
+        try:
+            t.build(keys, vals)
+        except G.GhtError as e:
+            return {"scheme": scheme, "n": n, "lf": lf, **cfg, "built": False, "status": e.status}
+        build_ms = _time_ms(lambda: t.build(keys, vals))
+        r = {"scheme": scheme, "n": n, "lf": lf, **cfg, "built": True,
+             "build_gkeys_s": round(n / build_ms / 1e6, 3)}
+        for f in fracs:
+            ms = _time_ms(lambda: t.find(qs[f], out))
+            r[f"find_gkeys_s_f{f}"] = round(n / ms / 1e6, 3)
+        tc = G.HashTable(scheme, n, lf, seed=seed, max_attempts=3, count_probes=1, **cfg)
+        tc.build(keys, vals)
+        r["insert_probes"] = round(tc.stats()["insert_probes"] / n, 4)
+        for f in fracs:
+            tc.reset_counters()
+            tc.find(qs[f], out)
+            r[f"find_probes_f{f}"] = round(tc.stats()["find_probes"] / n, 4)
+        if (scheme, lf) in PAPER_PROBES:
+            r["paper_probes_insert_pos_neg"] = PAPER_PROBES[(scheme, lf)]
+        return r
+
+    rows.append({"config": "bcht_n2^20_lf0.9_f0.5 (L2-resident)",
+                 **measure("bcht", 1 << 20, 0.9, (0.5,), SEED + 10)})
+    n = 1 << 24
+    for scheme, cfg in (("bcht", {}), ("p2bht", {}), ("iht", {}), ("cuckoo1", {}), ("cuckoo1", {"num_hashes": 4})):
+        for lf in (0.6, 0.8, 0.9, 0.95, 0.99):
+            rows.append({"config": "scheme_sweep_n2^24", **measure(scheme, n, lf, (0.0, 0.5, 1.0), SEED + 11, **cfg)})
+    for scheme, lf in (("p2bht", 0.86), ("iht", 0.86), ("bcht_lb", 0.9), ("bcht_lb", 0.99)):
+        rows.append({"config": "paper_points_n2^24", **measure(scheme, n, lf, (0.0, 1.0), SEED + 12)})
+    for scheme, cfg, lf in (("p2bht", {"bucket_size": 32}, 0.9), ("iht", {"bucket_size": 32}, 0.9)):
+        rows.append({"config": "b32_n2^24", **measure(scheme, n, lf, (0.0, 1.0), SEED + 13, **cfg)})
+    print(json.dumps({"metric": "scheme sweep: build/find Gkeys/s and probes per key", "workload": "sweep",
+                      "rows": rows}), flush=True)
+
+
+def run_success(args, world, rank, local):
+    """Success rate (Sec. VII-C): the same keys built with 200 different hash
+    constant sets per (scheme, load factor); the highest load factor still
+    building in >= 99 % of runs. One attempt per build (no retry)."""
+    import torch
+
+    import paper_2108_07232_gb300 as G
+    import workloads as W
+    from paper_2108_07232_gb300 import build as B
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+    n = 1 << 20
+    runs = 200
+    keys, vals = W.make_keys(n, SEED + 20, device=dev), W.make_values(n, SEED + 20, device=dev)
+    grid = {
+        "bcht": ({}, (0.95, 0.96, 0.97, 0.98, 0.99)),
+        "iht_b32": ({"bucket_size": 32}, (0.88, 0.89, 0.90, 0.91, 0.92, 0.93)),
+        "p2bht_b32": ({"bucket_size": 32}, (0.88, 0.89, 0.90, 0.91, 0.92, 0.93)),
+        "cuckoo1_h4": ({"num_hashes": 4}, (0.85, 0.86, 0.87, 0.88, 0.89, 0.90)),
+    }
+    res = {}
+    for name, (cfg, lfs) in grid.items():
+        scheme = name.split("_")[0]
+        res[name] = {}
+        for lf in lfs:
+            ok = 0
+            for r in range(runs):
+                t = G.HashTable(scheme, n, lf, seed=SEED + 1000 * r + 7, max_attempts=1, **cfg)
+                try:
+                    t.build(keys, vals)
+                    ok += 1
+                except G.GhtError:
+                    pass
+                del t
+            res[name][str(lf)] = ok / runs
+        passing = [lf for lf in lfs if res[name][str(lf)] >= 0.99]
+        res[name]["max_lf_at_99pct"] = max(passing) if passing else None
+    print(json.dumps({"metric": "build success rate over 200 hash-constant sets (2^20 keys)",
+                      "workload": "success", "paper_max_lf_at_99pct": {"bcht": 0.98, "iht_b32": 0.91,
+                                                                        "p2bht_b32": 0.91, "cuckoo1_h4": 0.88},
+                      "rates": res}), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -557,6 +692,12 @@ def main():
         return
     if args.workload == "served":
         run_served(args, world, rank, local)
+        return
+    if args.workload == "sweep":
+        run_sweep(args, world, rank, local)
+        return
+    if args.workload == "success":
+        run_success(args, world, rank, local)
         return
     run_ours(args, world, rank, local)
 
