@@ -205,22 +205,37 @@ bucketed_find_kernel(TableView tv, const uint32_t *__restrict__ queries, uint32_
 // inserts of a grouped build inside a small window of the table.
 struct PairQueue {
   uint64_t ba, bb, bc;  // input index of entry 0 of chunks a, b, c (warp-uniform)
+  uint64_t claim_next;  // dynamic mode: next chunk of the warp's current claim
+  uint32_t claim_left;  // chunks left in that claim
   int head;             // next unused entry of chunk a
   uint32_t ka, kb, kc, va, vb, vc;
 };
 
-__device__ __forceinline__ uint64_t claim_chunk(Ctrl *ctrl, int lane) {
-  unsigned long long x = 0ull;
-  if (lane == 0) x = atomicAdd(&ctrl->work_cursor, 32ull);
-  return __shfl_sync(kFull, x, 0);
+// Dynamic mode: a warp claims kClaimChunks consecutive 32-pair chunks at a
+// time from the global cursor (one atomic per claim, not per chunk).
+constexpr uint32_t kClaimChunks = 32;
+
+__device__ __forceinline__ uint64_t claim_chunk(PairQueue &q, Ctrl *ctrl, int lane) {
+  if (q.claim_left == 0) {
+    unsigned long long x = 0ull;
+    if (lane == 0) x = atomicAdd(&ctrl->work_cursor, 32ull * kClaimChunks);
+    q.claim_next = __shfl_sync(kFull, x, 0);
+    q.claim_left = kClaimChunks;
+  }
+  const uint64_t at = q.claim_next;
+  q.claim_next += 32;
+  q.claim_left--;
+  return at;
 }
 
 __device__ __forceinline__ void pair_init(PairQueue &q, const uint32_t *__restrict__ k, const uint32_t *__restrict__ v,
                                           uint64_t beg, uint64_t end, bool dynamic, Ctrl *ctrl, int lane) {
+  q.claim_next = 0;
+  q.claim_left = 0;
   if (dynamic) {
-    q.ba = claim_chunk(ctrl, lane);
-    q.bb = claim_chunk(ctrl, lane);
-    q.bc = claim_chunk(ctrl, lane);
+    q.ba = claim_chunk(q, ctrl, lane);
+    q.bb = claim_chunk(q, ctrl, lane);
+    q.bc = claim_chunk(q, ctrl, lane);
   } else {
     q.ba = beg;
     q.bb = beg + 32;
@@ -252,7 +267,7 @@ __device__ __forceinline__ uint64_t pair_take(PairQueue &q, const uint32_t *__re
     q.head -= 32;
     q.ba = q.bb;
     q.bb = q.bc;
-    q.bc = dynamic ? claim_chunk(ctrl, lane) : q.bc + 32;
+    q.bc = dynamic ? claim_chunk(q, ctrl, lane) : q.bc + 32;
     q.ka = q.kb;
     q.kb = q.kc;
     q.va = q.vb;

@@ -70,8 +70,10 @@ group_scan_kernel(const uint32_t *__restrict__ counts, uint32_t groups, uint32_t
 
 // Pass 2: scatter pairs to their group. Each block takes a tile of
 // kGroupTile pairs, ranks them per group in shared memory, reserves one
-// range per non-empty group with a single global atomic, then writes; the
-// pairs of a group within a tile land contiguously.
+// output range per non-empty group with a single global atomic, orders the
+// tile by group in shared memory, and then writes it with consecutive
+// threads storing consecutive items, so a group's items leave as one
+// contiguous run instead of scattered 4-byte stores.
 constexpr int kGroupPerThread = 16;
 constexpr int kGroupTile = 256 * kGroupPerThread;
 
@@ -80,33 +82,69 @@ group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint
                      uint64_t n, int shift, uint32_t groups, uint32_t *__restrict__ cursors,
                      uint32_t *__restrict__ out_k, uint32_t *__restrict__ out_v) {
   extern __shared__ uint32_t sh[];
-  uint32_t *cnt = sh, *base = sh + groups;
+  uint32_t *cnt = sh;                    // [groups] items of each group in the tile
+  uint32_t *pre = cnt + groups;          // [groups] exclusive prefix of cnt
+  uint32_t *base = pre + groups;         // [groups] reserved output position
+  uint32_t *sk = base + groups;          // [kGroupTile] tile keys ordered by group
+  uint32_t *sv = sk + kGroupTile;        // [kGroupTile] tile values
+  uint16_t *sg = reinterpret_cast<uint16_t *>(sv + kGroupTile);  // [kGroupTile] group of each ordered item
+  __shared__ uint32_t warp_sums[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (uint64_t t0 = (uint64_t)blockIdx.x * kGroupTile; t0 < n; t0 += (uint64_t)gridDim.x * kGroupTile) {
+    const uint32_t tile_n = (uint32_t)(n - t0 < (uint64_t)kGroupTile ? n - t0 : (uint64_t)kGroupTile);
     for (uint32_t i = threadIdx.x; i < groups; i += blockDim.x) cnt[i] = 0u;
     __syncthreads();
     uint32_t k[kGroupPerThread], v[kGroupPerThread], g[kGroupPerThread], rank[kGroupPerThread];
 #pragma unroll
     for (int u = 0; u < kGroupPerThread; ++u) {
-      const uint64_t i = t0 + (uint64_t)u * blockDim.x + threadIdx.x;  // coalesced reads
-      if (i < n) {
-        k[u] = __ldg(keys + i);
-        v[u] = __ldg(values + i);
+      const uint32_t i = (uint32_t)u * blockDim.x + threadIdx.x;  // coalesced reads
+      if (i < tile_n) {
+        k[u] = __ldg(keys + t0 + i);
+        v[u] = __ldg(values + t0 + i);
         g[u] = group_of(tv, k[u], shift);
         rank[u] = atomicAdd(&cnt[g[u]], 1u);
       }
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < groups; i += blockDim.x)
+    // exclusive prefix over the groups (each thread a contiguous run of them)
+    // and one output reservation per non-empty group
+    const uint32_t per = (groups + blockDim.x - 1) / blockDim.x;
+    const uint32_t g0 = threadIdx.x * per, g1 = g0 + per < groups ? g0 + per : groups;
+    uint32_t run = 0;
+    for (uint32_t i = g0; i < g1; ++i) run += cnt[i];
+    uint32_t incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_sums[wid] = incl;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int w = 0; w < wid; ++w) before += warp_sums[w];
+    uint32_t acc = before + incl - run;
+    for (uint32_t i = g0; i < g1; ++i) {
+      pre[i] = acc;
+      acc += cnt[i];
       if (cnt[i]) base[i] = atomicAdd(&cursors[i], cnt[i]);
+    }
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < kGroupPerThread; ++u) {
-      const uint64_t i = t0 + (uint64_t)u * blockDim.x + threadIdx.x;
-      if (i < n) {
-        const uint32_t at = base[g[u]] + rank[u];
-        out_k[at] = k[u];
-        out_v[at] = v[u];
+      const uint32_t i = (uint32_t)u * blockDim.x + threadIdx.x;
+      if (i < tile_n) {
+        const uint32_t at = pre[g[u]] + rank[u];
+        sk[at] = k[u];
+        sv[at] = v[u];
+        sg[at] = (uint16_t)g[u];
       }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < tile_n; i += blockDim.x) {
+      const uint32_t gi = sg[i];
+      const uint32_t at = base[gi] + (i - pre[gi]);
+      out_k[at] = sk[i];
+      out_v[at] = sv[i];
     }
     __syncthreads();
   }
@@ -129,8 +167,13 @@ cudaError_t launch_group(const TableView &tv, const uint32_t *keys, const uint32
   const uint64_t tiles = (n + kGroupTile - 1) / kGroupTile;
   e = grid_for(group_scatter_kernel, tiles * 256, 0, &blocks);
   if (e != cudaSuccess) return e;
-  group_scatter_kernel<<<blocks, 256, 2 * groups * sizeof(uint32_t), s>>>(tv, keys, values, n, shift, groups,
-                                                                         cursors, out_k, out_v);
+  const size_t smem = 3ull * groups * sizeof(uint32_t) + 2ull * kGroupTile * sizeof(uint32_t) +
+                      kGroupTile * sizeof(uint16_t);
+  if (smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(group_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  group_scatter_kernel<<<blocks, 256, smem, s>>>(tv, keys, values, n, shift, groups, cursors, out_k, out_v);
   return cudaGetLastError();
 }
 
