@@ -632,6 +632,8 @@ def run_sweep(args, world, rank, local):
         rows.append({"config": "paper_points_n2^24", **measure(scheme, n, lf, (0.0, 1.0), SEED + 12)})
     for scheme, cfg, lf in (("p2bht", {"bucket_size": 32}, 0.9), ("iht", {"bucket_size": 32}, 0.9)):
         rows.append({"config": "b32_n2^24", **measure(scheme, n, lf, (0.0, 1.0), SEED + 13, **cfg)})
+    for lf in (0.9, 0.99):
+        rows.append({"config": "keys_only_set_n2^24", **measure("bcht_set", n, lf, (0.0, 0.5, 1.0), SEED + 14)})
     print(json.dumps({"metric": "scheme sweep: build/find Gkeys/s and probes per key", "workload": "sweep",
                       "rows": rows}), flush=True)
 

@@ -10,6 +10,10 @@
  *   GHT_IHT      iceberg, b = 16, primary + two secondaries, t = 13 (Sec. III-C, V-D)
  *   GHT_CUCKOO1  bucket size one cuckoo ("1CHT"), three hash functions (Sec. VII)
  *   GHT_BCHT_LB  load-balanced bucketed cuckoo (Sec. III-A, last paragraph)
+ *   GHT_BCHT_SET keys-only bucketed cuckoo, a membership set: 32 four-byte keys
+ *                per 128-byte bucket, three hash functions (the tables "storing
+ *                keys" of Sec. I and Sec. III-A); values are not stored, a find
+ *                writes 1 for a present key and 0 for an absent one
  *
  * Conventions used by every entry point:
  *   - Keys and values are uint32. 0xFFFFFFFF (GHT_EMPTY) is the empty key and
@@ -50,7 +54,8 @@ typedef enum {
   GHT_P2BHT = 1,
   GHT_IHT = 2,
   GHT_CUCKOO1 = 3,
-  GHT_BCHT_LB = 4
+  GHT_BCHT_LB = 4,
+  GHT_BCHT_SET = 5
 } ght_scheme;
 
 typedef enum {
@@ -116,7 +121,7 @@ typedef struct {
    * yet complete) */
   double last_fill_ms, last_insert_ms, last_find_ms, last_group_ms;
   int32_t last_build_grouped;
-  int32_t pad0;
+  int32_t slot_bytes;          /* 8 for key/value pairs, 4 for GHT_BCHT_SET */
 } ght_stats_t;
 
 /* Library version string; never NULL. */
@@ -147,7 +152,8 @@ ght_table *ght_create_ex(int scheme, uint64_t capacity, double load_factor, uint
 /* Issue all later work on `cuda_stream` (a cudaStream_t; NULL = legacy default). */
 int ght_set_stream(ght_table *t, void *cuda_stream);
 
-/* Bulk build (Sec. III insertion of every key, Sec. V-B..D kernels): fill the
+/* Bulk build (Sec. III insertion of every key, Sec. V-B..D kernels); for
+ * GHT_BCHT_SET d_values is ignored and may be NULL. Fill the
  * table with empty pairs, insert the n pairs (d_keys[i], d_values[i]), read
  * the device status; on failure retry with the next attempt's constants, up
  * to max_attempts. n <= capacity (else GHT_ERR_CAPACITY). n = 0 builds an
@@ -207,8 +213,9 @@ int ght_stats(const ght_table *t, ght_stats_t *out);
 /* Zero the find counters. */
 int ght_reset_counters(ght_table *t);
 
-/* Copy the raw slot array (num_slots pairs, bucket-major) to host memory
- * h_slots of n_slots >= num_slots entries; synchronous. For validation. */
+/* Copy the raw slot array (num_slots slots of slot_bytes each, bucket-major)
+ * to host memory h_slots, which holds n_slots 8-byte words (enough for
+ * num_slots * slot_bytes bytes); synchronous. For validation. */
 int ght_export(const ght_table *t, uint64_t *h_slots, uint64_t n_slots);
 
 /* Bucket indices of each key under each of the table's hash functions,

@@ -13,7 +13,7 @@ them over torch tensors (int32 tensors carry the uint32 bit patterns).
 from __future__ import annotations
 
 from ._binding import (  # noqa: F401
-    BCHT, BCHT_LB, CUCKOO1, EMPTY, IHT, P2BHT, SCHEMES, Batch, GhtBatchStats, GhtConfig, GhtError, GhtStats,
+    BCHT, BCHT_LB, BCHT_SET, CUCKOO1, EMPTY, IHT, P2BHT, SCHEMES, Batch, GhtBatchStats, GhtConfig, GhtError, GhtStats,
     HashTable, Pool,
     ght_build, ght_build_host, ght_create, ght_create_ex, ght_default_config, ght_destroy,
     ght_export, ght_find, ght_find_host, ght_find_host_noalloc, ght_hash_device, ght_hash_host, ght_last_error,
@@ -22,6 +22,6 @@ from ._binding import (  # noqa: F401
 )
 
 __all__ = [
-    "BCHT", "P2BHT", "IHT", "CUCKOO1", "BCHT_LB", "EMPTY", "SCHEMES", "HashTable", "Batch", "Pool", "GhtError",
+    "BCHT", "P2BHT", "IHT", "CUCKOO1", "BCHT_LB", "BCHT_SET", "EMPTY", "SCHEMES", "HashTable", "Batch", "Pool", "GhtError",
     "GhtConfig", "GhtStats", "lib", "lib_path",
 ]

@@ -10,8 +10,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(HERE, "_build", "libght.so")
 
 EMPTY = 0xFFFFFFFF
-BCHT, P2BHT, IHT, CUCKOO1, BCHT_LB = 0, 1, 2, 3, 4
-SCHEMES = {"bcht": BCHT, "p2bht": P2BHT, "iht": IHT, "cuckoo1": CUCKOO1, "bcht_lb": BCHT_LB}
+BCHT, P2BHT, IHT, CUCKOO1, BCHT_LB, BCHT_SET = 0, 1, 2, 3, 4, 5
+SCHEMES = {"bcht": BCHT, "p2bht": P2BHT, "iht": IHT, "cuckoo1": CUCKOO1, "bcht_lb": BCHT_LB,
+           "bcht_set": BCHT_SET}
 
 STATUS = {
     0: "GHT_OK", 1: "GHT_ERR_INVALID_ARG", 2: "GHT_ERR_OOM", 3: "GHT_ERR_BUILD_FAILED",
@@ -48,7 +49,7 @@ class GhtStats(C.Structure):
         ("table_bytes", C.c_uint64), ("built", C.c_int32), ("tile_lanes", C.c_int32),
         ("keys_per_lane", C.c_int32), ("build_tile_lanes", C.c_int32), ("build_keys_per_lane", C.c_int32),
         ("last_fill_ms", C.c_double), ("last_insert_ms", C.c_double), ("last_find_ms", C.c_double),
-        ("last_group_ms", C.c_double), ("last_build_grouped", C.c_int32), ("pad0", C.c_int32),
+        ("last_group_ms", C.c_double), ("last_build_grouped", C.c_int32), ("slot_bytes", C.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -355,10 +356,17 @@ class HashTable:
             raise ValueError("tensors must be contiguous")
         return x
 
-    def build(self, keys, values) -> None:
-        k, v = self._u32(keys), self._u32(values)
-        if k.numel() != v.numel():
-            raise ValueError("keys and values differ in length")
+    def build(self, keys, values=None) -> None:
+        """Build from keys and values (values may be None for a keys-only set)."""
+        k = self._u32(keys)
+        if values is None:
+            if self.scheme != BCHT_SET:
+                raise ValueError("values are required except for a keys-only set")
+            v = None
+        else:
+            v = self._u32(values)
+            if k.numel() != v.numel():
+                raise ValueError("keys and values differ in length")
         with _device_of(self.device):
             self._stream()
             self._ensure_scratch(k.numel())
@@ -408,14 +416,15 @@ class HashTable:
         ght_reset_counters(self._t)
 
     def export(self):
-        """Raw slots (num_slots uint64 pairs, bucket-major) as a numpy array."""
+        """Raw slots, bucket-major, as a numpy array: uint64 pairs, or uint32
+        keys for a keys-only set."""
         import numpy as np
         s = ght_stats(self._t)
-        out = np.empty(s.num_slots, dtype=np.uint64)
+        out = np.empty(s.num_slots * s.slot_bytes // 8, dtype=np.uint64)
         with _device_of(self.device):
             self._stream()
             ght_export(self._t, out, out.size)
-        return out
+        return out.view(np.uint32) if s.slot_bytes == 4 else out
 
     def hash_device(self, keys):
         """(n, h) int64 tensor of bucket indices computed on the device."""

@@ -38,6 +38,7 @@ struct Shape {
   int tile_lanes, blocks_per_sm, keys_per_lane;                    // find
   int build_tile_lanes, build_blocks_per_sm, build_keys_per_lane;  // build
   int group_build;  // 1: group the input by first-choice bucket range before inserting
+  int slot_bytes;   // 8 (key/value pair) or 4 (keys-only set)
   uint64_t m;
 };
 
@@ -49,6 +50,7 @@ int default_config(int scheme, ght_config *c) {
     case GHT_IHT: c->bucket_size = 16; c->num_hashes = 3; c->threshold = 13; break;
     case GHT_CUCKOO1: c->bucket_size = 1; c->num_hashes = 3; c->max_chain = 1000; break;
     case GHT_BCHT_LB: c->bucket_size = 16; c->num_hashes = 3; c->max_chain = 1000; break;
+    case GHT_BCHT_SET: c->bucket_size = 32; c->num_hashes = 3; c->max_chain = 1000; break;
     default: return fail(GHT_ERR_INVALID_ARG, "unknown scheme %d", scheme);
   }
   c->max_attempts = 50;
@@ -86,7 +88,12 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
   }
   if (!(lf > 0.0) || !(lf <= 1.0)) return fail(GHT_ERR_INVALID_ARG, "load factor %g is not in (0, 1]", lf);
   const int b = d.bucket_size, h = d.num_hashes;
-  if (scheme == GHT_CUCKOO1) {
+  if (scheme == GHT_BCHT_SET) {
+    if (b != 32) return fail(GHT_ERR_INVALID_ARG, "the keys-only set has 32 keys per bucket");
+    if (h < 2 || h > 4) return fail(GHT_ERR_INVALID_ARG, "the keys-only set needs 2..4 hash functions");
+    for (int g : {d.tile_lanes, d.build_tile_lanes})
+      if (!ght::set_shape_supported(b, g)) return fail(GHT_ERR_INVALID_ARG, "tile of %d lanes unsupported for the set", g);
+  } else if (scheme == GHT_CUCKOO1) {
     if (b != 1) return fail(GHT_ERR_INVALID_ARG, "CUCKOO1 has bucket size 1");
     if (h < 2 || h > 4) return fail(GHT_ERR_INVALID_ARG, "CUCKOO1 needs 2..4 hash functions");
   } else {
@@ -121,13 +128,14 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
   s->build_tile_lanes = d.build_tile_lanes;
   s->build_blocks_per_sm = d.build_blocks_per_sm;
   s->build_keys_per_lane = d.build_keys_per_lane;
-  s->group_build = d.group_build;
+  s->group_build = scheme == GHT_BCHT_SET ? 0 : d.group_build;
+  s->slot_bytes = scheme == GHT_BCHT_SET ? 4 : 8;
   s->m = (uint64_t)want;
   return GHT_OK;
 }
 
 uint64_t bytes_of(const Shape &s) {
-  const uint64_t slots = s.m * (uint64_t)s.b * 8ull;
+  const uint64_t slots = s.m * (uint64_t)s.b * (uint64_t)s.slot_bytes;
   return kCtrlBytes + ((slots + 255ull) & ~255ull);
 }
 
@@ -180,6 +188,9 @@ struct ght_table {
     rng_seed = ght::host::derive_rng_seed(seed, attempt);
   }
 
+  // table size in 8-byte words (what the fill kernel writes)
+  uint64_t words() const { return shape.m * (uint64_t)shape.b * (uint64_t)shape.slot_bytes / 8ull; }
+
   ght::TableView view() const {
     ght::TableView v;
     v.slots = slots;
@@ -229,6 +240,7 @@ cudaError_t launch_insert(const ght_table *t, const uint32_t *k, const uint32_t 
   ght::LaunchOpts o = t->build_opts();
   o.dynamic = dynamic;
   if (t->shape.scheme == GHT_BCHT) return ght::launch_insert_bcht(t->shape.b, tv, k, v, n, o, t->stream);
+  if (t->shape.scheme == GHT_BCHT_SET) return ght::launch_insert_set(tv, k, v ? v : k, n, o, t->stream);
   return ght::launch_insert_other(t->shape.scheme, t->shape.b, tv, k, v, n, o, t->stream);
 }
 
@@ -244,6 +256,7 @@ bool wants_grouping(const ght_table *t, uint64_t n) {
 cudaError_t launch_find(const ght_table *t, const uint32_t *q, uint32_t *out, uint64_t n) {
   const ght::TableView tv = t->view();
   if (t->shape.scheme == GHT_BCHT) return ght::launch_find_bcht(t->shape.b, tv, q, out, n, t->find_opts(), t->stream);
+  if (t->shape.scheme == GHT_BCHT_SET) return ght::launch_find_set(tv, q, out, n, t->find_opts(), t->stream);
   return ght::launch_find_other(t->shape.scheme, t->shape.b, tv, q, out, n, t->find_opts(), t->stream);
 }
 
@@ -288,7 +301,7 @@ int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n,
     t->derive(attempt);
     const ght::TableView tv = t->view();
     cudaEventRecord(t->tev[0], t->stream);
-    cudaError_t e = ght::launch_fill(tv, t->shape.m * (uint64_t)t->shape.b, t->stream);
+    cudaError_t e = ght::launch_fill(tv, t->words(), t->stream);
     if (e != cudaSuccess) { rc = cuda_fail(e, "launching fill"); break; }
     cudaEventRecord(t->tev[1], t->stream);
     if (grouped) {
@@ -427,7 +440,8 @@ int ght_build(ght_table *t, const uint32_t *d_keys, const uint32_t *d_values, ui
   if (!t) return fail(GHT_ERR_INVALID_ARG, "table is NULL");
   if (n > t->capacity) return fail(GHT_ERR_CAPACITY, "n = %llu exceeds capacity %llu", (unsigned long long)n,
                                    (unsigned long long)t->capacity);
-  if (n > 0 && (!d_keys || !d_values)) return fail(GHT_ERR_INVALID_ARG, "keys or values is NULL");
+  if (n > 0 && (!d_keys || (!d_values && t->shape.scheme != GHT_BCHT_SET)))
+    return fail(GHT_ERR_INVALID_ARG, "keys or values is NULL");
   return build_device(t, d_keys, d_values, n, 0);
 }
 
@@ -448,8 +462,10 @@ int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_value
   if (!t) return fail(GHT_ERR_INVALID_ARG, "table is NULL");
   if (n > t->capacity) return fail(GHT_ERR_CAPACITY, "n = %llu exceeds capacity %llu", (unsigned long long)n,
                                    (unsigned long long)t->capacity);
-  if (n > 0 && (!h_keys || !h_values)) return fail(GHT_ERR_INVALID_ARG, "keys or values is NULL");
+  if (n > 0 && (!h_keys || (!h_values && t->shape.scheme != GHT_BCHT_SET)))
+    return fail(GHT_ERR_INVALID_ARG, "keys or values is NULL");
   if (n == 0) return build_device(t, nullptr, nullptr, 0, 0);
+  if (!h_values) h_values = h_keys;  // a set ignores values
   // Stage the pairs on the device (the library pool keeps the block for the
   // next call). An input-order build inserts each chunk as soon as it has
   // landed, overlapping the copies with the inserts of the first attempt;
@@ -483,7 +499,7 @@ int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_value
       t->derive(0);
       const ght::TableView tv = t->view();
       cudaEventRecord(t->tev[0], t->stream);
-      if ((e = ght::launch_fill(tv, t->shape.m * (uint64_t)t->shape.b, t->stream)) != cudaSuccess)
+      if ((e = ght::launch_fill(tv, t->words(), t->stream)) != cudaSuccess)
         rc = cuda_fail(e, "launching fill");
       cudaEventRecord(t->tev[1], t->stream);
       cudaEventRecord(t->tev[2], t->stream);
@@ -651,6 +667,7 @@ int ght_stats(const ght_table *t, ght_stats_t *out) {
   float ms = 0.f;
   out->last_group_ms = -1.0;
   out->last_build_grouped = t->last_grouped ? 1 : 0;
+  out->slot_bytes = t->shape.slot_bytes;
   if (t->timed_build && cudaEventQuery(t->tev[3]) == cudaSuccess) {
     if (cudaEventElapsedTime(&ms, t->tev[0], t->tev[1]) == cudaSuccess) out->last_fill_ms = ms;
     if (cudaEventElapsedTime(&ms, t->tev[1], t->tev[2]) == cudaSuccess) out->last_group_ms = ms;
@@ -677,10 +694,10 @@ int ght_reset_counters(ght_table *t) {
 
 int ght_export(const ght_table *t, uint64_t *h_slots, uint64_t n_slots) {
   if (!t || !h_slots) return fail(GHT_ERR_INVALID_ARG, "table or h_slots is NULL");
-  const uint64_t total = t->shape.m * (uint64_t)t->shape.b;
-  if (n_slots < total) return fail(GHT_ERR_INVALID_ARG, "h_slots holds %llu pairs, need %llu",
-                                   (unsigned long long)n_slots, (unsigned long long)total);
-  cudaError_t e = cudaMemcpyAsync(h_slots, t->slots, total * 8ull, cudaMemcpyDeviceToHost, t->stream);
+  const uint64_t words = t->words();
+  if (n_slots < words) return fail(GHT_ERR_INVALID_ARG, "h_slots holds %llu words, need %llu",
+                                   (unsigned long long)n_slots, (unsigned long long)words);
+  cudaError_t e = cudaMemcpyAsync(h_slots, t->slots, words * 8ull, cudaMemcpyDeviceToHost, t->stream);
   if (e != cudaSuccess) return cuda_fail(e, "exporting slots");
   e = cudaEventRecord(t->done, t->stream);
   if (e != cudaSuccess) return cuda_fail(e, "recording an event");

@@ -104,6 +104,27 @@ struct TableView {
 __device__ __forceinline__ uint32_t pair_key(uint64_t p) { return (uint32_t)p; }
 __device__ __forceinline__ uint32_t pair_value(uint64_t p) { return (uint32_t)(p >> 32); }
 
+// Slot kinds of a bucketed table. PairSlot: 64-bit (value << 32) | key, a
+// find returns the value or the sentinel. KeySlot: a 32-bit key only (a
+// membership set), a find returns 1 (present) or 0 (absent).
+struct PairSlot {
+  using T = unsigned long long;
+  static constexpr T kEmpty = 0xFFFFFFFFFFFFFFFFull;
+  __device__ static uint32_t key(T s) { return (uint32_t)s; }
+  __device__ static uint32_t found(T s) { return (uint32_t)(s >> 32); }
+  __device__ static T make(uint32_t k, uint32_t v) { return ((T)v << 32) | k; }
+  __device__ static uint32_t missing() { return kEmptyKey; }
+};
+
+struct KeySlot {
+  using T = unsigned int;
+  static constexpr T kEmpty = 0xFFFFFFFFu;
+  __device__ static uint32_t key(T s) { return s; }
+  __device__ static uint32_t found(T) { return 1u; }
+  __device__ static T make(uint32_t k, uint32_t) { return k; }
+  __device__ static uint32_t missing() { return 0u; }
+};
+
 // Marsaglia xorshift32 (13, 17, 5), "Xorshift RNGs" (2003), the eviction-slot
 // generator of Sec. V-B.
 __device__ __forceinline__ uint32_t xorshift32(uint32_t &s) {
@@ -168,6 +189,58 @@ __device__ __forceinline__ void load_part_rw(const uint64_t *bucket, int r, uint
       v[i + 1] = y;
     }
   }
+}
+
+// Generic part loads: lane r of a tile reads slots [r*PPL, (r+1)*PPL) of a
+// bucket of slot type T, with 16-byte vector loads when the part allows.
+template <int PPL, typename T>
+__device__ __forceinline__ void load_slots_ro(const T *bucket, int r, T (&v)[PPL]) {
+  if constexpr (sizeof(T) == 8) {
+    load_part_ro<PPL>(reinterpret_cast<const uint64_t *>(bucket), r, reinterpret_cast<uint64_t(&)[PPL]>(v));
+  } else {
+    static_assert(PPL % 4 == 0, "32-bit slots are read 4 at a time");
+    const uint4 *p = reinterpret_cast<const uint4 *>(bucket + r * PPL);
+#pragma unroll
+    for (int i = 0; i < PPL / 4; ++i) {
+      const uint4 x = __ldg(p + i);
+      v[4 * i] = x.x;
+      v[4 * i + 1] = x.y;
+      v[4 * i + 2] = x.z;
+      v[4 * i + 3] = x.w;
+    }
+  }
+}
+
+template <int PPL, typename T>
+__device__ __forceinline__ void load_slots_rw(const T *bucket, int r, T (&v)[PPL]) {
+  if constexpr (sizeof(T) == 8) {
+    load_part_rw<PPL>(reinterpret_cast<const uint64_t *>(bucket), r, reinterpret_cast<uint64_t(&)[PPL]>(v));
+  } else {
+    static_assert(PPL % 4 == 0, "32-bit slots are read 4 at a time");
+    const T *p = bucket + r * PPL;
+#pragma unroll
+    for (int i = 0; i < PPL; i += 4) {
+      unsigned a, b, c, d;
+      asm volatile("ld.relaxed.gpu.global.v4.b32 {%0, %1, %2, %3}, [%4];"
+                   : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
+                   : "l"(p + i)
+                   : "memory");
+      v[i] = a;
+      v[i + 1] = b;
+      v[i + 2] = c;
+      v[i + 3] = d;
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T cas_slot(T *slot, T expect, T desired) {
+  return atomicCAS(slot, expect, desired);
+}
+
+template <typename T>
+__device__ __forceinline__ T exch_slot(T *slot, T desired) {
+  return atomicExch(slot, desired);
 }
 
 __device__ __forceinline__ uint64_t cas_pair(uint64_t *slot, uint64_t expect, uint64_t desired) {

@@ -70,6 +70,13 @@ cudaError_t launch_find_bcht(int B, const TableView &tv, const uint32_t *q, uint
                              uint64_t n, const LaunchOpts &o, cudaStream_t s);
 bool bcht_shape_supported(int B, int G);
 
+// kern_set.cu (keys-only BCHT, 32 four-byte keys per bucket)
+bool set_shape_supported(int B, int G);
+cudaError_t launch_insert_set(const TableView &tv, const uint32_t *k, const uint32_t *v, uint64_t n,
+                              const LaunchOpts &o, cudaStream_t s);
+cudaError_t launch_find_set(const TableView &tv, const uint32_t *q, uint32_t *out, uint64_t n, const LaunchOpts &o,
+                            cudaStream_t s);
+
 // kern_other.cu
 cudaError_t launch_insert_other(int scheme, int B, const TableView &tv, const uint32_t *k,
                                 const uint32_t *v, uint64_t n, const LaunchOpts &o, cudaStream_t s);

@@ -75,11 +75,13 @@ __device__ __forceinline__ uint64_t stream_take(StreamQueue &q, const uint32_t *
 // one set's bucket reads are in flight while the other set is evaluated.
 // Tile members report a hit (and its value) or an empty slot to the owner
 // through per-warp shared memory rather than one ballot per slot.
-template <int SCHEME, int B, int G, int KPL, bool COUNT>
+template <int SCHEME, int B, int G, int KPL, bool COUNT, typename S = PairSlot>
 __global__ void __launch_bounds__(256)
 bucketed_find_kernel(TableView tv, const uint32_t *__restrict__ queries, uint32_t *__restrict__ out,
                      uint64_t n, uint64_t per_warp) {
+  using T = typename S::T;
   constexpr int PPL = B / G;
+  const T *slots = reinterpret_cast<const T *>(tv.slots);
   constexpr bool kEarlyExit = (SCHEME == kBCHT);
   static_assert(B % G == 0 && 32 % G == 0 && PPL >= 1 && (KPL == 1 || KPL == 2), "tile shape");
   __shared__ uint32_t s_hit[8][32], s_emp[8][32], s_val[8][32];
@@ -99,7 +101,7 @@ bucketed_find_kernel(TableView tv, const uint32_t *__restrict__ queries, uint32_
   uint32_t key[KPL], act[KPL];
   uint64_t idx[KPL];
   int probe[KPL];
-  uint64_t v[KPL][G][PPL];
+  T v[KPL][G][PPL];
 #pragma unroll
   for (int s = 0; s < KPL; ++s) {
     active[s] = false;
@@ -121,7 +123,7 @@ bucketed_find_kernel(TableView tv, const uint32_t *__restrict__ queries, uint32_
         if (at < end) {
           if (COUNT) answered++;
           if (k == kEmptyKey) {
-            out[at] = kEmptyKey;  // the sentinel is never a key
+            out[at] = S::missing();  // the sentinel is never a key
           } else {
             active[s] = true;
             key[s] = k;
@@ -136,7 +138,7 @@ bucketed_find_kernel(TableView tv, const uint32_t *__restrict__ queries, uint32_
 #pragma unroll
         for (int j = 0; j < G; ++j) {
           const uint32_t bj = __shfl_sync(kFull, myb, tbase + j);
-          if ((act[s] >> (tbase + j)) & 1u) load_part_ro<PPL>(tv.slots + (uint64_t)bj * B, r, v[s][j]);
+          if ((act[s] >> (tbase + j)) & 1u) load_slots_ro<PPL>(slots + (uint64_t)bj * B, r, v[s][j]);
         }
       }
       // evaluate the other set (or this one when KPL = 1)
@@ -152,10 +154,10 @@ bucketed_find_kernel(TableView tv, const uint32_t *__restrict__ queries, uint32_
           if ((act[e] >> owner) & 1u) {
 #pragma unroll
             for (int p = 0; p < PPL; ++p) {
-              const uint32_t sk = pair_key(v[e][j][p]);
+              const uint32_t sk = S::key(v[e][j][p]);
               if (sk == kj) {
                 s_hit[wib][owner] = 1u;
-                s_val[wib][owner] = pair_value(v[e][j][p]);
+                s_val[wib][owner] = S::found(v[e][j][p]);
               }
               if (kEarlyExit && sk == kEmptyKey) s_emp[wib][owner] = 1u;
             }
@@ -165,7 +167,7 @@ bucketed_find_kernel(TableView tv, const uint32_t *__restrict__ queries, uint32_
         if ((act[e] >> lane) & 1u) {
           if (COUNT) probes++;
           bool finish = false;
-          uint32_t result = kEmptyKey;
+          uint32_t result = S::missing();
           if (s_hit[wib][lane]) {
             result = s_val[wib][lane];
             finish = true;
@@ -301,11 +303,13 @@ __device__ __forceinline__ uint64_t pair_take(PairQueue &q, const uint32_t *__re
 // Each lane runs KPL independent slots. A slot's atomic result is inspected
 // only on the slot's next turn, so with KPL = 2 its latency is hidden behind
 // the other slot's bucket reads. per_warp = 0 selects dynamic chunks.
-template <int SCHEME, int B, int G, int KPL, bool COUNT>
+template <int SCHEME, int B, int G, int KPL, bool COUNT, typename S = PairSlot>
 __global__ void __launch_bounds__(256)
 bucketed_insert_kernel(TableView tv, const uint32_t *__restrict__ keys,
                        const uint32_t *__restrict__ values, uint64_t n, uint64_t per_warp) {
+  using T = typename S::T;
   constexpr int PPL = B / G;
+  T *slots = reinterpret_cast<T *>(tv.slots);
   static_assert(B % G == 0 && 32 % G == 0 && PPL >= 1 && (KPL == 1 || KPL == 2), "tile shape");
   const int lane = threadIdx.x & 31;
   const int r = lane & (G - 1);
@@ -325,7 +329,7 @@ bucketed_insert_kernel(TableView tv, const uint32_t *__restrict__ keys,
   pair_init(pq, keys, values, beg, end, dynamic, tv.ctrl, lane);
   // per-slot state
   bool active[KPL], retrying[KPL];
-  uint64_t pair[KPL], old[KPL];
+  T pair[KPL], old[KPL];
   uint32_t cur[KPL], chain[KPL], steps[KPL];
   int op[KPL], phase[KPL];
   // remembered reads: P2BHT (l_a, s_a, b_a) = H_0; IHT a = primary, b = H_s0;
@@ -356,7 +360,7 @@ bucketed_insert_kernel(TableView tv, const uint32_t *__restrict__ keys,
     for (int s = 0; s < KPL; ++s) {
       // -- resolve the atomic this slot issued on its previous turn
       if (op[s] == 1) {
-        if (old[s] == kEmptyPair) {
+        if (old[s] == S::kEmpty) {
           active[s] = false;  // stored
           if (COUNT && chain[s] > longest) longest = chain[s];
         } else {
@@ -364,18 +368,18 @@ bucketed_insert_kernel(TableView tv, const uint32_t *__restrict__ keys,
           if (SCHEME == kP2BHT || SCHEME == kIHT || SCHEME == kBCHT_LB) {
             phase[s] = 0;
             l_a[s] = B + 1;
-            cur[s] = bucket_of(tv.hf, 0, pair_key(pair[s]));
+            cur[s] = bucket_of(tv.hf, 0, S::key(pair[s]));
           }
         }
       } else if (op[s] == 2) {
         if (COUNT) evictions++;
         chain[s]++;
-        if (pair_key(old[s]) == kEmptyKey) {
+        if (S::key(old[s]) == kEmptyKey) {
           active[s] = false;  // the slot had been emptied -- cannot happen, but storing is complete
         } else if (SCHEME == kBCHT) {
           const uint32_t from = cur[s];
           pair[s] = old[s];
-          const uint32_t k = pair_key(old[s]);
+          const uint32_t k = S::key(old[s]);
           int i = -1;
 #pragma unroll
           for (int f = 0; f < 4; ++f)
@@ -391,7 +395,7 @@ bucketed_insert_kernel(TableView tv, const uint32_t *__restrict__ keys,
           b_b[s] = b_a[s];
           phase[s] = 0;
           l_a[s] = B + 1;
-          cur[s] = bucket_of(tv.hf, 0, pair_key(old[s]));
+          cur[s] = bucket_of(tv.hf, 0, S::key(old[s]));
         }
       }
       op[s] = 0;
@@ -405,7 +409,7 @@ bucketed_insert_kernel(TableView tv, const uint32_t *__restrict__ keys,
           if (k == kEmptyKey) {
             atomicOr(&tv.ctrl->status, kStatusSentinel);
           } else {
-            pair[s] = ((uint64_t)val << 32) | k;
+            pair[s] = S::make(k, val);
             active[s] = true;
             retrying[s] = false;
             chain[s] = 0;
@@ -421,11 +425,11 @@ bucketed_insert_kernel(TableView tv, const uint32_t *__restrict__ keys,
       if (act == 0u) continue;
 
       // -- gather one bucket per active lane of the tile
-      uint64_t v[G][PPL];
+      T v[G][PPL];
 #pragma unroll
       for (int j = 0; j < G; ++j) {
         const uint32_t bj = __shfl_sync(kFull, cur[s], tbase + j);
-        if ((act >> (tbase + j)) & 1u) load_part_rw<PPL>(tv.slots + (uint64_t)bj * B, r, v[j]);
+        if ((act >> (tbase + j)) & 1u) load_slots_rw<PPL>(slots + (uint64_t)bj * B, r, v[j]);
       }
       // owner learns how many slots are empty and where one of them is
       int my_empty = 0, my_slot = -1;
@@ -435,7 +439,7 @@ bucketed_insert_kernel(TableView tv, const uint32_t *__restrict__ keys,
         int cnt = 0, slot = -1;
 #pragma unroll
         for (int p = 0; p < PPL; ++p) {
-          const unsigned em = __ballot_sync(kFull, aj && pair_key(v[j][p]) == kEmptyKey) & tmask;
+          const unsigned em = __ballot_sync(kFull, aj && S::key(v[j][p]) == kEmptyKey) & tmask;
           cnt += __popc(em);
           if (slot < 0 && em) slot = (__ffs(em) - 1 - tbase) * PPL + p;
         }
@@ -446,14 +450,14 @@ bucketed_insert_kernel(TableView tv, const uint32_t *__restrict__ keys,
       }
 
       // -- decide and issue this slot's atomic
-      uint64_t *target = nullptr;
+      T *target = nullptr;
       if (active[s]) {
         if (COUNT) {
           if (retrying[s]) retries++;
           else probes++;
         }
         const int load = B - my_empty;
-        const uint32_t k = pair_key(pair[s]);
+        const uint32_t k = S::key(pair[s]);
         bool fail = false;
         if (++steps[s] > tv.max_steps) {
           atomicOr(&tv.ctrl->status, kStatusTimeout);
@@ -461,12 +465,12 @@ bucketed_insert_kernel(TableView tv, const uint32_t *__restrict__ keys,
         } else if (SCHEME == kBCHT) {
           if (load < B) {
             op[s] = 1;
-            target = tv.slots + (uint64_t)cur[s] * B + my_slot;
+            target = slots + (uint64_t)cur[s] * B + my_slot;
           } else if (chain[s] >= tv.max_chain) {
             fail = true;
           } else {
             op[s] = 2;
-            target = tv.slots + (uint64_t)cur[s] * B + (xorshift32(rng) % B);
+            target = slots + (uint64_t)cur[s] * B + (xorshift32(rng) % B);
           }
         } else if (SCHEME == kP2BHT) {
           if (phase[s] == 0) {
@@ -477,15 +481,15 @@ bucketed_insert_kernel(TableView tv, const uint32_t *__restrict__ keys,
             fail = true;
           } else {
             op[s] = 1;
-            target = (l_a[s] <= load) ? tv.slots + (uint64_t)b_a[s] * B + s_a[s]
-                                      : tv.slots + (uint64_t)cur[s] * B + my_slot;
+            target = (l_a[s] <= load) ? slots + (uint64_t)b_a[s] * B + s_a[s]
+                                      : slots + (uint64_t)cur[s] * B + my_slot;
           }
         } else if (SCHEME == kIHT) {
           if (phase[s] == 0) {
             l_a[s] = load; s_a[s] = my_slot; b_a[s] = cur[s];
             if (load + 1 < tv.t) {
               op[s] = 1;
-              target = tv.slots + (uint64_t)cur[s] * B + my_slot;
+              target = slots + (uint64_t)cur[s] * B + my_slot;
             } else {
               phase[s] = 1;
               cur[s] = bucket_of(tv.hf, 1, k);
@@ -496,11 +500,11 @@ bucketed_insert_kernel(TableView tv, const uint32_t *__restrict__ keys,
             cur[s] = bucket_of(tv.hf, 2, k);
           } else if (l_b[s] < B || load < B) {
             op[s] = 1;
-            target = (l_b[s] <= load) ? tv.slots + (uint64_t)b_b[s] * B + s_b[s]
-                                      : tv.slots + (uint64_t)cur[s] * B + my_slot;
+            target = (l_b[s] <= load) ? slots + (uint64_t)b_b[s] * B + s_b[s]
+                                      : slots + (uint64_t)cur[s] * B + my_slot;
           } else if (l_a[s] < B) {
             op[s] = 1;
-            target = tv.slots + (uint64_t)b_a[s] * B + s_a[s];
+            target = slots + (uint64_t)b_a[s] * B + s_a[s];
           } else {
             fail = true;
           }
@@ -513,12 +517,12 @@ bucketed_insert_kernel(TableView tv, const uint32_t *__restrict__ keys,
             cur[s] = bucket_of(tv.hf, phase[s], k);
           } else if (l_a[s] < B) {
             op[s] = 1;
-            target = tv.slots + (uint64_t)b_a[s] * B + s_a[s];
+            target = slots + (uint64_t)b_a[s] * B + s_a[s];
           } else if (l_a[s] > B || chain[s] >= tv.max_chain) {
             fail = true;  // no candidate besides the one it came from, or chain bound
           } else {
             op[s] = 2;
-            target = tv.slots + (uint64_t)b_a[s] * B + (xorshift32(rng) % B);
+            target = slots + (uint64_t)b_a[s] * B + (xorshift32(rng) % B);
           }
         }
         if (fail) {
@@ -529,8 +533,8 @@ bucketed_insert_kernel(TableView tv, const uint32_t *__restrict__ keys,
       }
       // at most one atomic per lane; a warp issues them together and the
       // results are read on the slot's next turn
-      if (op[s] == 1) old[s] = cas_pair(target, kEmptyPair, pair[s]);
-      else if (op[s] == 2) old[s] = exch_pair(target, pair[s]);
+      if (op[s] == 1) old[s] = cas_slot<T>(target, S::kEmpty, pair[s]);
+      else if (op[s] == 2) old[s] = exch_slot<T>(target, pair[s]);
       if (op[s] != 0) retrying[s] = false;
     }
     bool any = false;

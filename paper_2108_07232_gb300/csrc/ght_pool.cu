@@ -93,7 +93,7 @@ struct ght_pool {
   int device = 0;
   std::mutex mu;
   std::condition_variable cv_find, cv_build, cv_done;
-  std::vector<PoolTable> tables;
+  std::deque<PoolTable> tables;  // a deque: submit_build appends while workers hold references
   std::unordered_map<uint64_t, Req> reqs;
   std::deque<uint64_t> find_q, build_q;
   uint64_t next_ticket = 1;
@@ -286,6 +286,7 @@ void ght_pool::build_loop() {
   for (;;) {
     uint64_t tk = 0;
     Req r;
+    PoolTable *ptp = nullptr;  // element address taken under the lock (stable in a deque)
     {
       std::unique_lock<std::mutex> lock(mu);
       for (;;) {
@@ -309,13 +310,14 @@ void ght_pool::build_loop() {
             tables[head.table].state = kBuilding;
             head.t_start = now_s();
             r = head;
+            ptp = &tables[head.table];
             break;
           }
         }
         cv_build.wait_for(lock, std::chrono::milliseconds(2));
       }
     }
-    PoolTable &pt = tables[r.table];
+    PoolTable &pt = *ptp;
     int rc = GHT_OK;
     void *storage = nullptr;
     cudaError_t e = ght::host::pool_alloc(&storage, pt.bytes, build_stream);

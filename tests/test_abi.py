@@ -59,6 +59,13 @@ def test_table_bytes_follow_the_oracle_sizing(L, scheme, b):
         assert L.ght_table_bytes(scheme, n, lf) == 256 + ((slots + 255) // 256) * 256
 
 
+def test_keys_only_set_uses_four_byte_slots(L):
+    for n, lf in [(1 << 20, 0.9), (1000, 0.99), (0, 0.5)]:
+        m = O.num_buckets(n, lf, 32)
+        assert L.ght_table_bytes(5, n, lf) == 256 + ((m * 32 * 4 + 255) // 256) * 256
+    assert L.ght_table_bytes(5, 100, 0.9, {"bucket_size": 16}) == 0
+
+
 def test_table_bytes_rejects_bad_shapes(L):
     assert L.ght_table_bytes(0, 100, 0.0) == 0
     assert L.ght_table_bytes(0, 100, 1.01) == 0
