@@ -138,6 +138,23 @@ class ClockSampler:
                 "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the find
+# kernel, averaged over its four launches of one step of the default workload,
+# from one ncu capture (profiles/bcht_find_n2e28_traffic.md). It describes the
+# kernel source it was captured from, identified by a hash of the kernel
+# headers; after any change to them the traffic is reported as null.
+FIND_TRAFFIC = {"bytes_per_launch": 60371993856, "source_sha256_16": "d3f5158cd9132f24"}
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("ght_kernels.cuh", "ght_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2108_07232_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def bytes_per_key(op: str, p: float, lf: float) -> float:
     """Algorithmic bytes per key (query/result or pair, 128 B per bucket probe,
     plus one write-back of the table for inserts)."""
@@ -340,8 +357,14 @@ def run_ours(args, world, rank, local):
                        "frac_of_hbm": round(byts / (t_ms / 1e3) / 1e9 / peak, 4)}
     dom_name = max(per_func, key=lambda f: per_func[f]["ms_per_step"])
     dom = per_func[dom_name]
+    traffic = None
+    if (dom_name == "bucketed_find_kernel" and args.log2n == 28
+            and kernel_source_hash() == FIND_TRAFFIC["source_sha256_16"]):
+        traffic = FIND_TRAFFIC["bytes_per_launch"]
+    alg_per_launch = sum(kernels[k]["bytes_per_key"] * n for k in funcs[dom_name]) / len(funcs[dom_name])
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": dom["achieved_gbs"], "peak": peak,
-                "unit": "GB/s", "frac": dom["frac_of_hbm"], "traffic": None,
+                "unit": "GB/s", "frac": dom["frac_of_hbm"], "traffic": traffic,
+                "algorithmic_bytes_per_launch": round(alg_per_launch),
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s",
                 "note": "achieved = algorithmic bytes of the kernel's launches in one step / their summed CUDA-event time"}
 
