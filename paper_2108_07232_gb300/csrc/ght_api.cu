@@ -42,6 +42,29 @@ struct Shape {
   uint64_t m;
 };
 
+// Launch shapes measured fastest on GB300 at 2^27-2^28 keys (insert with
+// dynamic chunk claims; load factors near each scheme's working range).
+// Finds read 16-pair buckets fastest with two queries in flight per lane
+// and 32-pair buckets with one; builds the other way round, except the
+// keys-only set, fastest with one key per lane for both. BCHT reads a
+// 16-pair bucket with 4 lanes in its finds and 16 in its inserts; every
+// other bucketed kernel uses 8.
+void default_shape(int scheme, int b, ght_config *c) {
+  if (scheme == GHT_CUCKOO1) {
+    c->tile_lanes = c->build_tile_lanes = 1;
+    c->keys_per_lane = c->build_keys_per_lane = 1;
+    return;
+  }
+  c->tile_lanes = scheme == GHT_BCHT && b == 16 ? 4 : 8;
+  c->build_tile_lanes = scheme == GHT_BCHT && b == 16 ? 16 : 8;
+  if (scheme == GHT_BCHT_SET) {
+    c->keys_per_lane = c->build_keys_per_lane = 1;
+  } else {
+    c->keys_per_lane = b == 16 ? 2 : 1;
+    c->build_keys_per_lane = b == 16 ? 1 : 2;
+  }
+}
+
 int default_config(int scheme, ght_config *c) {
   memset(c, 0, sizeof *c);
   switch (scheme) {
@@ -54,13 +77,7 @@ int default_config(int scheme, ght_config *c) {
     default: return fail(GHT_ERR_INVALID_ARG, "unknown scheme %d", scheme);
   }
   c->max_attempts = 50;
-  // tile shapes: measured defaults for 16-pair BCHT buckets on GB300; 8 lanes
-  // elsewhere (the only shape instantiated for the other schemes)
-  const bool bcht16 = scheme == GHT_BCHT;
-  c->tile_lanes = scheme == GHT_CUCKOO1 ? 1 : (bcht16 ? 4 : 8);
-  c->keys_per_lane = 2;
-  c->build_tile_lanes = scheme == GHT_CUCKOO1 ? 1 : (bcht16 ? 16 : 8);
-  c->build_keys_per_lane = bcht16 ? 1 : 2;
+  default_shape(scheme, c->bucket_size, c);
   return GHT_OK;
 }
 
@@ -74,7 +91,7 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
     if (user->num_hashes) d.num_hashes = user->num_hashes;
     if (user->max_chain) d.max_chain = user->max_chain;
     if (user->max_attempts) d.max_attempts = user->max_attempts;
-    if (user->bucket_size == 32 && scheme == GHT_BCHT) d.tile_lanes = d.build_tile_lanes = 8;
+    default_shape(scheme, d.bucket_size, &d);
     if (user->tile_lanes) d.tile_lanes = user->tile_lanes;
     if (user->build_tile_lanes) d.build_tile_lanes = user->build_tile_lanes;
     d.count_probes = user->count_probes;
@@ -234,11 +251,14 @@ struct ght_table {
 
 namespace {
 
-cudaError_t launch_insert(const ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n,
-                          bool dynamic = false) {
+// Insert n pairs. The warps claim runs of 32-pair chunks from the control
+// block's work cursor, which must be zero at launch (the fill clears it), so
+// that the warps finish together however long the eviction chains of their
+// keys are; a static slice per warp left a slow tail of 15-30 % at 2^28 keys.
+cudaError_t launch_insert(const ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n) {
   const ght::TableView tv = t->view();
   ght::LaunchOpts o = t->build_opts();
-  o.dynamic = dynamic;
+  o.dynamic = true;
   if (t->shape.scheme == GHT_BCHT) return ght::launch_insert_bcht(t->shape.b, tv, k, v, n, o, t->stream);
   if (t->shape.scheme == GHT_BCHT_SET) return ght::launch_insert_set(tv, k, v ? v : k, n, o, t->stream);
   return ght::launch_insert_other(t->shape.scheme, t->shape.b, tv, k, v, n, o, t->stream);
@@ -310,7 +330,7 @@ int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n,
     }
     cudaEventRecord(t->tev[2], t->stream);
     if (n > 0) {
-      e = grouped ? launch_insert(t, gk, gv, n, true) : launch_insert(t, k, v, n);
+      e = grouped ? launch_insert(t, gk, gv, n) : launch_insert(t, k, v, n);
       if (e != cudaSuccess) { rc = cuda_fail(e, "launching insert"); break; }
     }
     cudaEventRecord(t->tev[3], t->stream);
@@ -512,7 +532,10 @@ int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_value
           rc = cuda_fail(e, "staging keys");
           break;
         }
-        if ((e = launch_insert(t, d_k + off, d_v + off, len)) != cudaSuccess) rc = cuda_fail(e, "launching insert");
+        // each chunk's insert starts its own claims at zero
+        if ((e = cudaMemsetAsync(&t->ctrl->work_cursor, 0, sizeof t->ctrl->work_cursor, t->stream)) != cudaSuccess ||
+            (e = launch_insert(t, d_k + off, d_v + off, len)) != cudaSuccess)
+          rc = cuda_fail(e, "launching insert");
       }
       cudaEventRecord(t->tev[3], t->stream);
       t->timed_build = true;
