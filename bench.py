@@ -41,8 +41,15 @@ def parse():
     ap.add_argument("--log2n", type=int, default=28, help="keys per table (log2)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ceilings", action="store_true", help="skip the memory-pattern ceiling probe")
     ap.add_argument("--tile-lanes", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--build-tile-lanes", type=int, default=0)
+    ap.add_argument("--group-build", type=int, default=0, choices=[-1, 0, 1],
+                    help="1: group the pairs by first-choice bucket range before the build")
+    ap.add_argument("--ranked-build", type=int, default=0, choices=[-1, 0],
+                    help="BCHT build: 0 two-phase (ranked first-choice placement, then cuckoo insert), "
+                         "-1 cuckoo insert of every key")
     ap.add_argument("--workload", choices=["hbm", "batched", "served", "sweep", "success"], default="hbm",
                     help="hbm: 2^28-key BCHT tables (default); batched: 512 uneven tables in one graph "
                          "launch; served: a table pool under Poisson request arrivals")
@@ -141,15 +148,15 @@ class ClockSampler:
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the find
 # kernel, averaged over its four launches of one step of the default workload,
 # from one ncu capture (profiles/bcht_find_n2e28_traffic.md). It describes the
-# kernel source it was captured from, identified by a hash of the kernel
-# headers; after any change to them the traffic is reported as null.
+# kernel source it was captured from, identified by a hash of the find
+# kernel's headers; after any change to them the traffic is reported as null.
 FIND_TRAFFIC = {"bytes_per_launch": 60374900032, "source_sha256_16": "d54d51a32b04541d"}
 
 
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("ght_kernels.cuh", "ght_device.cuh"):
+    for f in ("ght_find.cuh", "ght_device.cuh"):
         with open(os.path.join(ROOT, "paper_2108_07232_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -165,6 +172,38 @@ def bytes_per_key(op: str, p: float, lf: float) -> float:
     if op == "fill":
         return 8 / lf
     raise ValueError(op)
+
+
+PROBE_MODES = {0: "random_line_read", 1: "line_read_then_cas", 2: "line_read_then_cas_waited", 3: "atomic_add_only"}
+
+
+def measure_ceilings(num_lines: int, ops: int, dev, reps: int = 3) -> dict:
+    """Rates of the tables' memory access patterns on random 128-byte lines of
+    a buffer as large as the table (ght_probe_lines), untimed by the step."""
+    import torch
+
+    import paper_2108_07232_gb300 as G
+    buf = torch.empty(num_lines * 128 // 8, dtype=torch.int64, device=dev)
+    buf.fill_(-1)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    out = {}
+    for mode, name in PROBE_MODES.items():
+        G.ght_probe_lines(mode, buf, num_lines, ops, 7, stream)  # warm
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for r in range(reps):
+            G.ght_probe_lines(mode, buf, num_lines, ops, 11 + r, stream)
+        e1.record()
+        e1.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3 / reps
+        out[name] = {"glines_s": round(ops / sec / 1e9, 2), "ms": round(sec * 1e3, 3),
+                     "line_gbs": round(128 * ops / sec / 1e9, 1)}
+    del buf
+    torch.cuda.empty_cache()
+    out["note"] = (f"{ops} operations on random lines of a {num_lines * 128 / 1e9:.2f} GB buffer; line_gbs counts "
+                   "128 B per operation (the atomic-only mode touches 8 B)")
+    return out
 
 
 # ------------------------------------------------------------- CPU oracle ---
@@ -258,18 +297,26 @@ def run_ours(args, world, rank, local):
         cfg["tile_lanes"] = args.tile_lanes
     if args.blocks_per_sm:
         cfg["blocks_per_sm"] = args.blocks_per_sm
+    if args.build_tile_lanes:
+        cfg["build_tile_lanes"] = args.build_tile_lanes
+    if args.ranked_build:
+        cfg["ranked_build"] = args.ranked_build
+    if args.group_build:
+        cfg["group_build"] = args.group_build
     tables = {lf: G.HashTable("bcht", n, lf, seed=seed, **cfg) for lf in LFS}
     torch.cuda.synchronize()
 
     launches = [0]
-    phase_ms = {f"{op}@{lf}": [] for lf in LFS for op in ("fill", "insert", "find_pos", "find_neg")}
+    phase_ms = {f"{op}@{lf}": [] for lf in LFS for op in ("fill", "group", "place", "insert", "find_pos", "find_neg")}
 
     def step(record: bool):
         for lf in LFS:
             t = tables[lf]
             t.build(keys, vals)
             st = t.stats()
-            launches[0] += 2 * st["attempts"]
+            # fill + (grouping: count, scan, scatter) + (ranked placement) + cuckoo insert per attempt
+            launches[0] += (2 + (1 if st["last_build_ranked"] else 0)
+                            + (3 if st["last_build_grouped"] else 0)) * st["attempts"]
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e2 = torch.cuda.Event(enable_timing=True)
@@ -281,6 +328,8 @@ def run_ours(args, world, rank, local):
             launches[0] += 2
             if record:
                 phase_ms[f"fill@{lf}"].append(st["last_fill_ms"])
+                phase_ms[f"group@{lf}"].append(max(st["last_group_ms"], 0.0))
+                phase_ms[f"place@{lf}"].append(max(st["last_place_ms"], 0.0))
                 phase_ms[f"insert@{lf}"].append(st["last_insert_ms"])
                 e2.synchronize()
                 phase_ms[f"find_pos@{lf}"].append(e0.elapsed_time(e1))
@@ -334,8 +383,14 @@ def run_ours(args, world, rank, local):
 
     peak, peak_src = peaks()
     kernels = {}
+    st0 = tables[LFS[0]].stats()
+    ranked, grouped = bool(st0["last_build_ranked"]), bool(st0["last_build_grouped"])
     for lf in LFS:
-        for op, key, pp in (("fill", "fill", 0.0), ("insert", "insert", probes[lf]["insert"]),
+        # a build's work after the fill: the grouping and the ranked placement
+        # (when the build does them) and the cuckoo insert, timed together
+        phase_ms[f"build@{lf}"] = [a + b + c for a, b, c in zip(phase_ms[f"group@{lf}"], phase_ms[f"place@{lf}"],
+                                                               phase_ms[f"insert@{lf}"])]
+        for op, key, pp in (("fill", "fill", 0.0), ("insert", "build", probes[lf]["insert"]),
                             ("find", "find_pos", probes[lf]["find_pos"]),
                             ("find", "find_neg", probes[lf]["find_neg"])):
             t_ms = statistics.median(phase_ms[f"{key}@{lf}"])
@@ -345,8 +400,10 @@ def run_ours(args, world, rank, local):
                                       "bytes_per_key": round(bpk, 2), "achieved_gbs": round(gbs, 1),
                                       "frac_of_hbm": round(gbs / peak, 4)}
     # dominant kernel = the kernel function with the most device time per step
+    build_name = "+".join((["group_count_kernel", "group_scatter_kernel"] if grouped else [])
+                          + (["rank_place_kernel"] if ranked else []) + ["bucketed_insert_kernel"])
     funcs = {"bucketed_find_kernel": [k for k in kernels if k.startswith("find")],
-             "bucketed_insert_kernel": [k for k in kernels if k.startswith("insert")],
+             build_name: [k for k in kernels if k.startswith("build")],
              "fill_kernel": [k for k in kernels if k.startswith("fill")]}
     per_func = {}
     for f, ks in funcs.items():
@@ -368,6 +425,14 @@ def run_ours(args, world, rank, local):
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s",
                 "note": "achieved = algorithmic bytes of the kernel's launches in one step / their summed CUDA-event time"}
 
+    ceilings = None
+    if not args.no_ceilings:
+        ceilings = measure_ceilings(tables[LFS[0]].stats()["num_buckets"], n, dev)
+        ins_lines = sum(probes[lf]["insert"] * n for lf in LFS) / sum(kernels[f"build@{lf}"]["ms"] / 1e3 for lf in LFS)
+        find_lines = (sum((probes[lf]["find_pos"] + probes[lf]["find_neg"]) * n for lf in LFS)
+                      / sum((kernels[f"find_pos@{lf}"]["ms"] + kernels[f"find_neg@{lf}"]["ms"]) / 1e3 for lf in LFS))
+        ceilings["kernels_glines_s"] = {"find": round(find_lines / 1e9, 2), "insert": round(ins_lines / 1e9, 2)}
+
     # end to end through the public API from pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -375,12 +440,18 @@ def run_ours(args, world, rank, local):
         hp, hn = pos.cpu().pin_memory(), neg.cpu().pin_memory()
         hout = torch.empty_like(hk).pin_memory()
 
+        call_ms = {f"{op}@{lf}": [] for lf in LFS for op in ("build", "find_pos", "find_neg")}
+
         def host_step():
+            # each call returns once its results are on the host, so the wall
+            # time of each is its end-to-end time
             for lf in LFS:
                 t = tables[lf]
-                t.build(hk, hv)
-                t.find(hp, hout)
-                t.find(hn, hout)
+                for op, fn in (("build", lambda: t.build(hk, hv)), ("find_pos", lambda: t.find(hp, hout)),
+                               ("find_neg", lambda: t.find(hn, hout))):
+                    c0 = time.perf_counter()
+                    fn()
+                    call_ms[f"{op}@{lf}"].append(1e3 * (time.perf_counter() - c0))
             return int(hout[0])  # the step's result is on the host
 
         host_step()
@@ -395,7 +466,8 @@ def run_ours(args, world, rank, local):
         e2e = {"value": whole_job_value(keys_per_step, args.steps, world, 1e3 * el), "unit": "Gkeys/s",
                "h2d_bytes_per_step": len(LFS) * (8 * n + 8 * n),
                "d2h_bytes_per_step": len(LFS) * 8 * n,
-               "api": "HashTable.build/find on pinned CPU tensors (ght_build_host / ght_find_host)"}
+               "api": "HashTable.build/find on pinned CPU tensors (ght_build_host / ght_find_host)",
+               "call_ms": {k: round(statistics.median(v), 3) for k, v in call_ms.items()}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -413,6 +485,9 @@ def run_ours(args, world, rank, local):
             "data": "synthetic", "config": config_of(args), "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clocks,
             "kernels": kernels, "kernel_functions": per_func, "probes_per_key": probes,
+            "build_phases_ms": {str(lf): {ph: round(statistics.median(phase_ms[f"{ph}@{lf}"]), 4)
+                                         for ph in ("fill", "group", "place", "insert")} for lf in LFS},
+            "pattern_ceilings": ceilings,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -91,13 +91,21 @@ typedef struct {
   int32_t build_tile_lanes;
   int32_t build_keys_per_lane;
   int32_t build_blocks_per_sm;
-  /* Grouped build (opt-in, 1): the pairs are first regrouped by first-choice
-   * bucket range (H_0(k) >> s) and inserted group after group, so concurrent
-   * inserts touch a small window of the table. Needs scratch
-   * (ght_build_scratch_bytes), else the build inserts in input order. 0 or
-   * -1: input order (default). */
+  /* Grouped build: the pairs are first regrouped by first-choice bucket
+   * range (H_0(k) >> s), so the build's concurrent stores and atomics stay in
+   * a few MB of the table at a time. 1 = on, -1 = off, 0 = default: on for
+   * BCHT and BCHT_SET tables of at least 4x the device's L2 size. Needs
+   * scratch (ght_build_scratch_bytes), else the build runs in input order. */
   int32_t group_build;
-  int32_t reserved[3];
+  /* Two-phase build of BCHT and BCHT_SET: every key that arrives at its
+   * first-choice bucket while it has room is stored at its arrival rank
+   * without reading the bucket, the rest are inserted by the cuckoo insert
+   * (the same BCHT, Sec. III-A, with those keys inserted first). 1 = on,
+   * -1 = off, 0 = default: on when the build is grouped. Needs scratch
+   * (ght_build_scratch_bytes), else the build runs the cuckoo insert for
+   * every key. */
+  int32_t ranked_build;
+  int32_t reserved[2];
 } ght_config;
 
 typedef struct {
@@ -122,6 +130,10 @@ typedef struct {
   double last_fill_ms, last_insert_ms, last_find_ms, last_group_ms;
   int32_t last_build_grouped;
   int32_t slot_bytes;          /* 8 for key/value pairs, 4 for GHT_BCHT_SET */
+  int32_t last_build_ranked;   /* 1 if the last build was two-phase (ranked placement first) */
+  double last_place_ms;        /* device time of its ranked placement, with the grouping before it
+                                  when grouped (-1 if not two-phase) */
+  uint64_t place_overflow;     /* keys the ranked placement left to the cuckoo insert */
 } ght_stats_t;
 
 /* Library version string; never NULL. */
@@ -226,6 +238,21 @@ int ght_hash_device(const ght_table *t, const uint32_t *d_keys, uint32_t *d_buck
  * h_out[i] = ((a * h_keys[i] + c) mod p) mod m, for 1 <= m < 2^32. */
 int ght_hash_host(uint32_t a, uint32_t c, uint32_t m, const uint32_t *h_keys, uint32_t *h_out,
                   uint64_t n);
+
+/* Memory-system ceiling probe (a measurement aid; the paper has no
+ * counterpart). Runs `ops` operations on random 128-byte lines of d_lines
+ * (num_lines lines, caller-owned device memory, 128-byte aligned, contents
+ * are modified in modes 1-3), asynchronously on `cuda_stream` (NULL = legacy
+ * default stream). The line of operation i is a mixer of (seed, i) mod
+ * num_lines. Modes, after the access patterns of Sec. V:
+ *   0  read the whole line (a find's bucket probe, Sec. V-A/V-B);
+ *   1  read the line, then one 64-bit CAS into its first slot that depends on
+ *      the data read (an insert's probe and CAS, Sec. V-B), results unused;
+ *   2  as 1, and each step's CAS results are consumed before the next
+ *      step's reads (one atomic round trip per read);
+ *   3  one 64-bit atomic add into a random line, no read.
+ * Time it with events on the same stream. num_lines must be in [1, 2^32-1]. */
+int ght_probe_lines(int mode, void *d_lines, uint64_t num_lines, uint64_t ops, uint32_t seed, void *cuda_stream);
 
 /* Release the table (and its storage, if library-owned). NULL is a no-op. */
 void ght_destroy(ght_table *t);

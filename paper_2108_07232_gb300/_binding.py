@@ -34,7 +34,8 @@ class GhtConfig(C.Structure):
         ("max_chain", C.c_uint32), ("max_attempts", C.c_uint32), ("count_probes", C.c_int32),
         ("tile_lanes", C.c_int32), ("blocks_per_sm", C.c_int32), ("keys_per_lane", C.c_int32),
         ("build_tile_lanes", C.c_int32), ("build_keys_per_lane", C.c_int32),
-        ("build_blocks_per_sm", C.c_int32), ("group_build", C.c_int32), ("reserved", C.c_int32 * 3),
+        ("build_blocks_per_sm", C.c_int32), ("group_build", C.c_int32), ("ranked_build", C.c_int32),
+        ("reserved", C.c_int32 * 2),
     ]
 
 
@@ -50,6 +51,7 @@ class GhtStats(C.Structure):
         ("keys_per_lane", C.c_int32), ("build_tile_lanes", C.c_int32), ("build_keys_per_lane", C.c_int32),
         ("last_fill_ms", C.c_double), ("last_insert_ms", C.c_double), ("last_find_ms", C.c_double),
         ("last_group_ms", C.c_double), ("last_build_grouped", C.c_int32), ("slot_bytes", C.c_int32),
+        ("last_build_ranked", C.c_int32), ("last_place_ms", C.c_double), ("place_overflow", C.c_uint64),
     ]
 
     def as_dict(self) -> dict:
@@ -143,6 +145,7 @@ def lib():
                 "ght_export": ([vp, vp, u64], i32),
                 "ght_hash_device": ([vp, vp, vp, u64], i32),
                 "ght_hash_host": ([u32, u32, u32, vp, vp, u64], i32),
+                "ght_probe_lines": ([i32, vp, u64, u64, u32, vp], i32),
                 "ght_destroy": ([vp], None),
                 "ght_batch_create": ([C.c_uint32, vp, vp, u64, C.POINTER(GhtConfig)], vp),
                 "ght_batch_set_stream": ([vp, vp], i32),
@@ -292,6 +295,11 @@ def ght_hash_host(a: int, c: int, m: int, h_keys, h_out, n: int) -> None:
     _check(lib().ght_hash_host(a, c, m, _ptr(h_keys), _ptr(h_out), n))
 
 
+def ght_probe_lines(mode: int, d_lines, num_lines: int, ops: int, seed: int = 1, stream: int = 0) -> None:
+    """Memory-system ceiling probe on random 128-byte lines (asynchronous on `stream`)."""
+    _check(lib().ght_probe_lines(mode, _ptr(d_lines), num_lines, ops, seed, stream))
+
+
 def ght_destroy(t: int) -> None:
     lib().ght_destroy(t)
 
@@ -376,7 +384,7 @@ class HashTable:
                 ght_build_host(self._t, k, v, k.numel())
 
     def _ensure_scratch(self, n: int) -> None:
-        """Grouped builds need scratch; it is a torch tensor kept with the table."""
+        """Two-phase and grouped builds need scratch; it is a torch tensor kept with the table."""
         import torch
         need = ght_build_scratch_bytes(self._t, n)
         have = getattr(self, "_scratch_bytes", 0)
@@ -387,7 +395,7 @@ class HashTable:
             self._scratch_bytes = need
 
     def release_scratch(self) -> None:
-        """Drop the grouping scratch (later large builds run ungrouped until re-set)."""
+        """Drop the build scratch (later builds insert every key with the cuckoo insert until re-set)."""
         if getattr(self, "_scratch_bytes", 0):
             ght_set_build_scratch(self._t, None, 0)
             self._scratch = None

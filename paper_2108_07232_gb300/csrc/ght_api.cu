@@ -38,6 +38,7 @@ struct Shape {
   int tile_lanes, blocks_per_sm, keys_per_lane;                    // find
   int build_tile_lanes, build_blocks_per_sm, build_keys_per_lane;  // build
   int group_build;  // 1: group the input by first-choice bucket range before inserting
+  int ranked_build;  // 1: two-phase build (ranked first-choice placement, then cuckoo insert)
   int slot_bytes;   // 8 (key/value pair) or 4 (keys-only set)
   uint64_t m;
 };
@@ -100,6 +101,7 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
     if (user->keys_per_lane) d.keys_per_lane = user->keys_per_lane;
     if (user->build_keys_per_lane) d.build_keys_per_lane = user->build_keys_per_lane;
     d.group_build = user->group_build;
+    d.ranked_build = user->ranked_build;
     if (user->threshold) d.threshold = user->threshold;
     else if (scheme == GHT_IHT) d.threshold = (4 * d.bucket_size + 4) / 5;  // ceil(0.8 b)
   }
@@ -145,7 +147,9 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
   s->build_tile_lanes = d.build_tile_lanes;
   s->build_blocks_per_sm = d.build_blocks_per_sm;
   s->build_keys_per_lane = d.build_keys_per_lane;
-  s->group_build = scheme == GHT_BCHT_SET ? 0 : d.group_build;
+  s->group_build = d.group_build;
+  // ranked placement applies to the cuckoo tables with buckets (BCHT and the set)
+  s->ranked_build = (scheme == GHT_BCHT || scheme == GHT_BCHT_SET) ? d.ranked_build : -1;
   s->slot_bytes = scheme == GHT_BCHT_SET ? 4 : 8;
   s->m = (uint64_t)want;
   return GHT_OK;
@@ -171,6 +175,27 @@ uint64_t group_scratch_bytes(uint64_t n) {
   return head + 2 * arr;
 }
 
+// Overflow list capacity of a two-phase build of n keys: far above the ~10 %
+// of keys that overflow their first-choice bucket at load factor 1 with
+// 16-slot buckets; a larger overflow (many keys sharing a bucket) falls back
+// to the cuckoo insert of every key.
+uint64_t place_cap(uint64_t n) { return std::min<uint64_t>(n, n / 4 + 1024); }
+
+uint64_t align256(uint64_t x) { return (x + 255ull) & ~255ull; }
+
+uint64_t place_scratch_bytes(uint64_t m, uint64_t n) {
+  return align256(m * sizeof(uint32_t)) + 2 * align256(place_cap(n) * sizeof(uint32_t));
+}
+
+ght::PlaceBuffers place_buffers(char *scr, uint64_t m, uint64_t n) {
+  ght::PlaceBuffers pb;
+  pb.counters = reinterpret_cast<uint32_t *>(scr);
+  pb.cap = place_cap(n);
+  pb.ovf_k = reinterpret_cast<uint32_t *>(scr + align256(m * sizeof(uint32_t)));
+  pb.ovf_v = pb.ovf_k + align256(pb.cap * sizeof(uint32_t)) / sizeof(uint32_t);
+  return pb;
+}
+
 }  // namespace
 
 struct ght_table {
@@ -191,11 +216,14 @@ struct ght_table {
   uint32_t attempts = 0;
   ght::Ctrl *h_ctrl = nullptr;  // pinned mirror of the control block
   cudaEvent_t done = nullptr;
-  // timing events: fill start, fill end, grouping end, insert end, find start, find end
-  cudaEvent_t tev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  // timing events: fill start, fill end, pre-insert work end (grouping and/or ranked placement),
+  // insert end, find start, find end, grouping end (when a grouped build also places by rank)
+  cudaEvent_t tev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   bool timed_build = false;
   bool last_grouped = false;
-  void *scratch = nullptr;  // caller-owned grouping scratch (ght_set_build_scratch)
+  bool last_ranked = false;
+  uint64_t place_overflow = 0;
+  void *scratch = nullptr;  // caller-owned build scratch (ght_set_build_scratch)
   uint64_t scratch_bytes = 0;
   mutable bool timed_find = false;
   mutable uint64_t insert_probes = 0, insert_retries = 0, insert_evictions = 0, longest_chain = 0;
@@ -264,13 +292,69 @@ cudaError_t launch_insert(const ght_table *t, const uint32_t *k, const uint32_t 
   return ght::launch_insert_other(t->shape.scheme, t->shape.b, tv, k, v, n, o, t->stream);
 }
 
-// Whether a build of n keys groups its input first (opt-in: on GB300 the
-// grouping pass costs more than the locality saves, see the design notes);
-// it also needs scratch (caller-set, or the library pool when the library
-// owns the table storage).
+// L2 size of the current device (bytes; cached per device).
+uint64_t device_l2_bytes() {
+  static std::mutex mu;
+  static uint64_t cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 128ull << 20;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!cache[dev]) {
+    int l2 = 0;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess || l2 <= 0) {
+      cudaGetLastError();
+      l2 = 128 << 20;
+    }
+    cache[dev] = (uint64_t)l2;
+  }
+  return cache[dev];
+}
+
+// Whether a build of n keys groups its input first by first-choice bucket
+// range (config group_build: 1 on, -1 off, 0 by table size); it also needs
+// scratch (caller-set, or the library pool when the library owns the table
+// storage), else the build runs in input order.
 bool wants_grouping(const ght_table *t, uint64_t n) {
   if (t->shape.scheme == GHT_CUCKOO1 || n == 0 || n > 0xFFFFFFFFull) return false;
-  return t->shape.group_build > 0;
+  if (t->shape.group_build != 0) return t->shape.group_build > 0;
+  // default: cuckoo tables with buckets far larger than the L2, where the
+  // grouped two-phase build measured 1.3-1.4x faster than the insert of
+  // every key in input order (2^28 keys); at 2^20-2^24 keys it was slower
+  if (t->shape.scheme != GHT_BCHT && t->shape.scheme != GHT_BCHT_SET) return false;
+  return t->storage_bytes >= 4ull * device_l2_bytes();
+}
+
+// Whether a build of n keys runs in two phases (ranked first-choice
+// placement, then the cuckoo insert of the overflow).
+bool wants_ranked(const ght_table *t, uint64_t n) {
+  if (t->shape.ranked_build < 0 || n == 0 || n > 0xFFFFFFFFull) return false;
+  // default: with the grouping, whose order keeps the placement's stores in L2
+  return t->shape.ranked_build > 0 || wants_grouping(t, n);
+}
+
+uint64_t build_scratch_need(const ght_table *t, uint64_t n) {
+  return (wants_grouping(t, n) ? group_scratch_bytes(n) : 0) + (wants_ranked(t, n) ? place_scratch_bytes(t->shape.m, n) : 0);
+}
+
+// Scratch of a two- or grouped-phase build: the caller's, else (for tables on
+// library storage) the library pool; NULL if neither is available.
+char *build_scratch(ght_table *t, uint64_t need, void **pool_buf) {
+  *pool_buf = nullptr;
+  if (t->scratch && t->scratch_bytes >= need) return static_cast<char *>(t->scratch);
+  if (t->owns_storage && pool_alloc(pool_buf, need, t->stream) == cudaSuccess) return static_cast<char *>(*pool_buf);
+  cudaGetLastError();
+  *pool_buf = nullptr;
+  return nullptr;
+}
+
+cudaError_t launch_place(const ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n,
+                         const ght::PlaceBuffers &pb) {
+  const bool count = t->shape.count_probes != 0;
+  if (t->shape.scheme == GHT_BCHT_SET) return ght::launch_place_set(t->view(), k, n, pb, count, t->stream);
+  return ght::launch_place_bcht(t->shape.b, t->view(), k, v, n, pb, count, t->stream);
 }
 
 cudaError_t launch_find(const ght_table *t, const uint32_t *q, uint32_t *out, uint64_t n) {
@@ -294,19 +378,13 @@ int read_ctrl(const ght_table *t) {
 int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n, uint32_t first_attempt) {
   t->built = false;
   t->n_stored = 0;
+  bool ranked = wants_ranked(t, n);
   bool grouped = wants_grouping(t, n);
   void *pool_buf = nullptr;
   char *scr = nullptr;
-  if (grouped) {
-    const uint64_t need = group_scratch_bytes(n);
-    if (t->scratch && t->scratch_bytes >= need) {
-      scr = static_cast<char *>(t->scratch);
-    } else if (t->owns_storage && pool_alloc(&pool_buf, need, t->stream) == cudaSuccess) {
-      scr = static_cast<char *>(pool_buf);
-    } else {
-      cudaGetLastError();
-      grouped = false;  // no scratch: build in input order
-    }
+  if (ranked || grouped) {
+    scr = build_scratch(t, build_scratch_need(t, n), &pool_buf);
+    if (!scr) ranked = grouped = false;  // no scratch: the cuckoo insert of every key in input order
   }
   int shift = 0;
   uint32_t groups = 1;
@@ -315,6 +393,9 @@ int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n,
   uint32_t *cursors = counts + ght::kMaxGroups;
   uint32_t *gk = reinterpret_cast<uint32_t *>(scr + 2ull * ght::kMaxGroups * sizeof(uint32_t));
   uint32_t *gv = gk + (((n * sizeof(uint32_t) + 255ull) & ~255ull) / sizeof(uint32_t));
+  // scratch layout: [grouping: counts, cursors, keys, values][ranked placement]
+  const ght::PlaceBuffers pb =
+      ranked ? place_buffers(scr + (grouped ? group_scratch_bytes(n) : 0), t->shape.m, n) : ght::PlaceBuffers();
   int rc = fail(GHT_ERR_BUILD_FAILED, "build failed in %u attempts (chain bound or full buckets)",
                 t->shape.max_attempts);
   for (uint32_t attempt = first_attempt; attempt < t->shape.max_attempts; ++attempt) {
@@ -324,18 +405,55 @@ int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n,
     cudaError_t e = ght::launch_fill(tv, t->words(), t->stream);
     if (e != cudaSuccess) { rc = cuda_fail(e, "launching fill"); break; }
     cudaEventRecord(t->tev[1], t->stream);
+    const uint32_t *ik = k, *iv = v;  // what the cuckoo insert takes
+    uint64_t in = n;
+    bool this_ranked = false;
+    t->place_overflow = 0;
     if (grouped) {
-      e = ght::launch_group(tv, k, v, n, shift, groups, counts, cursors, gk, gv, t->stream);
+      e = ght::launch_group(tv, k, v ? v : k, n, shift, groups, counts, cursors, gk, gv, t->stream);
       if (e != cudaSuccess) { rc = cuda_fail(e, "launching grouping"); break; }
+      ik = gk;
+      iv = gv;
+      cudaEventRecord(t->tev[6], t->stream);
     }
-    cudaEventRecord(t->tev[2], t->stream);
-    if (n > 0) {
-      e = grouped ? launch_insert(t, gk, gv, n) : launch_insert(t, k, v, n);
+    if (ranked) {
+      // phase 1: ranked first-choice placement (of the grouped pairs, when
+      // grouped: the stores then stay in a few MB of the table, whose lines
+      // fill up in L2); its overflow goes to phase 2
+      if ((e = cudaMemsetAsync(pb.counters, 0, t->shape.m * sizeof(uint32_t), t->stream)) != cudaSuccess ||
+          (e = launch_place(t, ik, iv, n, pb)) != cudaSuccess) {
+        rc = cuda_fail(e, "launching the ranked placement");
+        break;
+      }
+      cudaEventRecord(t->tev[2], t->stream);
+      if ((rc = read_ctrl(t)) != GHT_OK) break;
+      if (t->h_ctrl->status & ght::kStatusSentinel) { rc = fail(GHT_ERR_SENTINEL_KEY, "an input key is the sentinel 0xFFFFFFFF"); break; }
+      const uint64_t ovf = t->h_ctrl->reserved[0];
+      t->place_overflow = ovf;
+      if (ovf <= pb.cap) {
+        this_ranked = true;
+        ik = pb.ovf_k;
+        iv = pb.ovf_v;
+        in = ovf;
+      } else {
+        // too many keys share first-choice buckets for the overflow list:
+        // start over and insert every key (grouped, if it was) with the cuckoo insert
+        cudaEventRecord(t->tev[0], t->stream);
+        if ((e = ght::launch_fill(tv, t->words(), t->stream)) != cudaSuccess) { rc = cuda_fail(e, "launching fill"); break; }
+        cudaEventRecord(t->tev[1], t->stream);
+        cudaEventRecord(t->tev[2], t->stream);
+      }
+    } else {
+      cudaEventRecord(t->tev[2], t->stream);
+    }
+    if (in > 0) {
+      e = launch_insert(t, ik, iv, in);
       if (e != cudaSuccess) { rc = cuda_fail(e, "launching insert"); break; }
     }
     cudaEventRecord(t->tev[3], t->stream);
     t->timed_build = true;
     t->last_grouped = grouped;
+    t->last_ranked = this_ranked;
     rc = read_ctrl(t);
     if (rc) break;
     const uint32_t st = t->h_ctrl->status;
@@ -435,7 +553,7 @@ ght_table *ght_create_ex(int scheme, uint64_t capacity, double load_factor, uint
   t->slots = reinterpret_cast<uint64_t *>(reinterpret_cast<char *>(t->storage) + kCtrlBytes);
   cudaError_t e = cudaMallocHost(reinterpret_cast<void **>(&t->h_ctrl), kCtrlBytes);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->done, cudaEventDisableTiming);
-  for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreate(&t->tev[i]);
+  for (int i = 0; i < 7 && e == cudaSuccess; ++i) e = cudaEventCreate(&t->tev[i]);
   if (e != cudaSuccess) {
     cuda_fail(e, "creating table resources");
     ght_destroy(t);
@@ -487,9 +605,10 @@ int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_value
   if (n == 0) return build_device(t, nullptr, nullptr, 0, 0);
   if (!h_values) h_values = h_keys;  // a set ignores values
   // Stage the pairs on the device (the library pool keeps the block for the
-  // next call). An input-order build inserts each chunk as soon as it has
-  // landed, overlapping the copies with the inserts of the first attempt;
-  // later attempts, and grouped builds, run from the staged copy.
+  // next call). The first attempt works on each chunk as soon as it has
+  // landed, overlapping the copies with the ranked placement (two-phase
+  // build) or with the inserts (input-order build); later attempts, and
+  // grouped builds, run from the staged copy.
   void *buf = nullptr;
   const uint64_t arr = (n * sizeof(uint32_t) + 255ull) & ~255ull;
   cudaError_t e = pool_alloc(&buf, 2 * arr, t->stream);
@@ -499,12 +618,20 @@ int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_value
   }
   uint32_t *d_k = static_cast<uint32_t *>(buf), *d_v = d_k + arr / sizeof(uint32_t);
   int rc = GHT_OK;
-  if (wants_grouping(t, n)) {
+  // From host buffers the input-order build overlaps the copies with the
+  // inserts chunk by chunk, which a grouped build cannot (the grouping needs
+  // every pair); so here grouping and ranked placement run only on request.
+  const bool ranked_wanted = t->shape.ranked_build > 0 && wants_ranked(t, n);
+  if (t->shape.group_build > 0 && wants_grouping(t, n)) {
     if ((e = cudaMemcpyAsync(d_k, h_keys, n * 4, cudaMemcpyHostToDevice, t->stream)) != cudaSuccess ||
         (e = cudaMemcpyAsync(d_v, h_values, n * 4, cudaMemcpyHostToDevice, t->stream)) != cudaSuccess)
       rc = cuda_fail(e, "staging keys");
     if (rc == GHT_OK) rc = build_device(t, d_k, d_v, n, 0);
   } else {
+    void *place_pool = nullptr;
+    char *scr = ranked_wanted ? build_scratch(t, place_scratch_bytes(t->shape.m, n), &place_pool) : nullptr;
+    const bool ranked = scr != nullptr;
+    const ght::PlaceBuffers pb = ranked ? place_buffers(scr, t->shape.m, n) : ght::PlaceBuffers();
     cudaStream_t copy = nullptr;
     cudaEvent_t landed[2] = {nullptr, nullptr};
     if ((e = cudaStreamCreateWithFlags(&copy, cudaStreamNonBlocking)) != cudaSuccess ||
@@ -513,16 +640,22 @@ int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_value
         (e = cudaEventRecord(landed[0], t->stream)) != cudaSuccess ||  // staging block allocated
         (e = cudaStreamWaitEvent(copy, landed[0], 0)) != cudaSuccess)
       rc = cuda_fail(e, "creating the copy pipeline");
+    bool retry_staged = false;   // build again from the staged copy, first attempt
+    bool retry_next = false;     // build again from the staged copy, next attempt
     if (rc == GHT_OK) {
       t->built = false;
       t->n_stored = 0;
+      t->place_overflow = 0;
       t->derive(0);
       const ght::TableView tv = t->view();
       cudaEventRecord(t->tev[0], t->stream);
       if ((e = ght::launch_fill(tv, t->words(), t->stream)) != cudaSuccess)
         rc = cuda_fail(e, "launching fill");
+      if (rc == GHT_OK && ranked &&
+          (e = cudaMemsetAsync(pb.counters, 0, t->shape.m * sizeof(uint32_t), t->stream)) != cudaSuccess)
+        rc = cuda_fail(e, "clearing the arrival counters");
       cudaEventRecord(t->tev[1], t->stream);
-      cudaEventRecord(t->tev[2], t->stream);
+      if (!ranked) cudaEventRecord(t->tev[2], t->stream);
       for (uint64_t off = 0, i = 0; rc == GHT_OK && off < n; off += kChunk, ++i) {
         const uint64_t len = std::min(kChunk, n - off);
         cudaEvent_t ev = landed[i & 1];
@@ -532,16 +665,34 @@ int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_value
           rc = cuda_fail(e, "staging keys");
           break;
         }
-        // each chunk's insert starts its own claims at zero
-        if ((e = cudaMemsetAsync(&t->ctrl->work_cursor, 0, sizeof t->ctrl->work_cursor, t->stream)) != cudaSuccess ||
-            (e = launch_insert(t, d_k + off, d_v + off, len)) != cudaSuccess)
-          rc = cuda_fail(e, "launching insert");
+        if (ranked) {
+          // each chunk's placement claims its tiles from zero; the overflow count accumulates
+          if ((e = cudaMemsetAsync(&t->ctrl->reserved[1], 0, sizeof t->ctrl->reserved[1], t->stream)) != cudaSuccess ||
+              (e = launch_place(t, d_k + off, d_v + off, len, pb)) != cudaSuccess)
+            rc = cuda_fail(e, "launching the ranked placement");
+        } else if ((e = cudaMemsetAsync(&t->ctrl->work_cursor, 0, sizeof t->ctrl->work_cursor, t->stream)) != cudaSuccess ||
+                   (e = launch_insert(t, d_k + off, d_v + off, len)) != cudaSuccess) {
+          rc = cuda_fail(e, "launching insert");  // each chunk's insert starts its own claims at zero
+        }
+      }
+      if (rc == GHT_OK && ranked) {
+        // phase 2: the cuckoo insert of the keys whose first-choice bucket was full
+        cudaEventRecord(t->tev[2], t->stream);
+        rc = read_ctrl(t);
+        if (rc == GHT_OK && !(t->h_ctrl->status & ght::kStatusSentinel)) {
+          const uint64_t ovf = t->h_ctrl->reserved[0];
+          t->place_overflow = ovf;
+          if (ovf > pb.cap) retry_staged = true;  // overflow list too small: build_device falls back
+          else if (ovf > 0 && (e = launch_insert(t, pb.ovf_k, pb.ovf_v, ovf)) != cudaSuccess)
+            rc = cuda_fail(e, "launching insert");
+        }
       }
       cudaEventRecord(t->tev[3], t->stream);
       t->timed_build = true;
       t->last_grouped = false;
-      if (rc == GHT_OK) rc = read_ctrl(t);
-      if (rc == GHT_OK) {
+      t->last_ranked = ranked && !retry_staged;
+      if (rc == GHT_OK && !retry_staged) rc = read_ctrl(t);
+      if (rc == GHT_OK && !retry_staged) {
         const uint32_t st = t->h_ctrl->status;
         t->attempts = 1;
         t->insert_probes = t->h_ctrl->insert_probes;
@@ -558,7 +709,7 @@ int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_value
         } else if (st & ght::kStatusCorrupt) {
           rc = fail(GHT_ERR_CUDA, "table corrupt: an evicted key did not hash to its bucket");
         } else {
-          rc = build_device(t, d_k, d_v, n, 1);  // the staged copy is complete: the stream waited on it
+          retry_next = true;
         }
       }
     }
@@ -566,6 +717,9 @@ int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_value
     if (landed[0]) cudaEventDestroy(landed[0]);
     if (landed[1]) cudaEventDestroy(landed[1]);
     if (copy) cudaStreamDestroy(copy);
+    if (place_pool) cudaFreeAsync(place_pool, t->stream);
+    // the staged copy is complete: the table stream waited on every chunk
+    if (rc == GHT_OK && (retry_staged || retry_next)) rc = build_device(t, d_k, d_v, n, retry_next ? 1 : 0);
   }
   cudaFreeAsync(buf, t->stream);
   if (rc == GHT_OK) {
@@ -647,7 +801,7 @@ uint64_t ght_build_scratch_bytes(const ght_table *t, uint64_t n) {
     fail(GHT_ERR_INVALID_ARG, "table is NULL");
     return 0;
   }
-  return wants_grouping(t, n) ? group_scratch_bytes(n) : 0;
+  return build_scratch_need(t, n);
 }
 
 int ght_set_build_scratch(ght_table *t, void *d_scratch, uint64_t bytes) {
@@ -691,9 +845,19 @@ int ght_stats(const ght_table *t, ght_stats_t *out) {
   out->last_group_ms = -1.0;
   out->last_build_grouped = t->last_grouped ? 1 : 0;
   out->slot_bytes = t->shape.slot_bytes;
+  out->last_build_ranked = t->last_ranked ? 1 : 0;
+  out->last_place_ms = -1.0;
+  out->place_overflow = t->place_overflow;
   if (t->timed_build && cudaEventQuery(t->tev[3]) == cudaSuccess) {
     if (cudaEventElapsedTime(&ms, t->tev[0], t->tev[1]) == cudaSuccess) out->last_fill_ms = ms;
-    if (cudaEventElapsedTime(&ms, t->tev[1], t->tev[2]) == cudaSuccess) out->last_group_ms = ms;
+    // between the fill and the cuckoo insert: the grouping and/or the ranked placement
+    if (t->last_grouped && t->last_ranked) {
+      if (cudaEventElapsedTime(&ms, t->tev[1], t->tev[6]) == cudaSuccess) out->last_group_ms = ms;
+      if (cudaEventElapsedTime(&ms, t->tev[6], t->tev[2]) == cudaSuccess) out->last_place_ms = ms;
+    } else if (cudaEventElapsedTime(&ms, t->tev[1], t->tev[2]) == cudaSuccess) {
+      if (t->last_ranked) out->last_place_ms = ms;
+      else if (t->last_grouped) out->last_group_ms = ms;
+    }
     if (cudaEventElapsedTime(&ms, t->tev[2], t->tev[3]) == cudaSuccess) out->last_insert_ms = ms;
   }
   if (t->timed_find && cudaEventQuery(t->tev[5]) == cudaSuccess &&
@@ -745,6 +909,17 @@ int ght_hash_host(uint32_t a, uint32_t c, uint32_t m, const uint32_t *h_keys, ui
   hf.mod = ght::make_fastmod(m);
   for (uint64_t i = 0; i < n; ++i) h_out[i] = ght::bucket_of(hf, 0, h_keys[i]);
   return GHT_OK;
+}
+
+int ght_probe_lines(int mode, void *d_lines, uint64_t num_lines, uint64_t ops, uint32_t seed, void *cuda_stream) {
+  if (mode < 0 || mode > 3) return fail(GHT_ERR_INVALID_ARG, "probe mode %d (0..3)", mode);
+  if (!d_lines || (reinterpret_cast<uintptr_t>(d_lines) & 127u))
+    return fail(GHT_ERR_INVALID_ARG, "lines must be a 128-byte aligned device pointer");
+  if (num_lines == 0 || num_lines > 0xFFFFFFFFull) return fail(GHT_ERR_INVALID_ARG, "num_lines outside [1, 2^32-1]");
+  if (ops == 0) return GHT_OK;
+  const cudaError_t e =
+      ght::launch_line_probe(mode, d_lines, num_lines, ops, seed, static_cast<cudaStream_t>(cuda_stream));
+  return e == cudaSuccess ? GHT_OK : cuda_fail(e, "launching the line probe");
 }
 
 void ght_destroy(ght_table *t) {

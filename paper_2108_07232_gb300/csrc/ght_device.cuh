@@ -233,6 +233,25 @@ __device__ __forceinline__ void load_slots_rw(const T *bucket, int r, T (&v)[PPL
   }
 }
 
+// Keys only of slots [r*PPL, (r+1)*PPL) of a bucket, for inserts, which need
+// to know which slots are empty and nothing else. For one 64-bit pair per
+// lane this loads the key word alone: half the registers per load in flight,
+// the same sectors.
+template <int PPL, typename T>
+__device__ __forceinline__ void load_keys_rw(const T *bucket, int r, uint32_t (&k)[PPL]) {
+  if constexpr (sizeof(T) == 8 && PPL == 1) {
+    const uint32_t *p = reinterpret_cast<const uint32_t *>(bucket + r);  // key = low word
+    uint32_t x;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(x) : "l"(p) : "memory");
+    k[0] = x;
+  } else {
+    T v[PPL];
+    load_slots_rw<PPL>(bucket, r, v);
+#pragma unroll
+    for (int i = 0; i < PPL; ++i) k[i] = (uint32_t)v[i];
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ T cas_slot(T *slot, T expect, T desired) {
   return atomicCAS(slot, expect, desired);

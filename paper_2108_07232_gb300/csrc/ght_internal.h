@@ -63,7 +63,18 @@ inline uint64_t per_warp_of(uint64_t n, int blocks) {
   return (n + warps - 1) / warps;
 }
 
+// Scratch of a two-phase (ranked placement) build: one arrival counter per
+// bucket and an overflow list of `cap` pairs (see rank_place_kernel).
+struct PlaceBuffers {
+  uint32_t *counters = nullptr;
+  uint32_t *ovf_k = nullptr;
+  uint32_t *ovf_v = nullptr;
+  uint64_t cap = 0;
+};
+
 // kern_bcht.cu
+cudaError_t launch_place_bcht(int B, const TableView &tv, const uint32_t *k, const uint32_t *v, uint64_t n,
+                              const PlaceBuffers &pb, bool count, cudaStream_t s);
 cudaError_t launch_insert_bcht(int B, const TableView &tv, const uint32_t *k, const uint32_t *v,
                                uint64_t n, const LaunchOpts &o, cudaStream_t s);
 cudaError_t launch_find_bcht(int B, const TableView &tv, const uint32_t *q, uint32_t *out,
@@ -71,6 +82,8 @@ cudaError_t launch_find_bcht(int B, const TableView &tv, const uint32_t *q, uint
 bool bcht_shape_supported(int B, int G);
 
 // kern_set.cu (keys-only BCHT, 32 four-byte keys per bucket)
+cudaError_t launch_place_set(const TableView &tv, const uint32_t *k, uint64_t n, const PlaceBuffers &pb, bool count,
+                             cudaStream_t s);
 bool set_shape_supported(int B, int G);
 cudaError_t launch_insert_set(const TableView &tv, const uint32_t *k, const uint32_t *v, uint64_t n,
                               const LaunchOpts &o, cudaStream_t s);
@@ -86,6 +99,10 @@ bool other_shape_supported(int scheme, int B, int G);
 cudaError_t launch_fill(const TableView &tv, uint64_t num_slots, cudaStream_t s);
 cudaError_t launch_hash(const TableView &tv, const uint32_t *k, uint32_t *out, uint64_t n,
                         cudaStream_t s);
+
+// kern_probe.cu: memory-system ceiling probe (see ght_probe_lines)
+cudaError_t launch_line_probe(int mode, void *lines, uint64_t num_lines, uint64_t ops, uint32_t seed,
+                              cudaStream_t s);
 
 // kern_group.cu: reorder (keys, values) by H_0(k) >> shift into out_k/out_v.
 cudaError_t launch_group(const TableView &tv, const uint32_t *keys, const uint32_t *values, uint64_t n,

@@ -1,203 +1,21 @@
-// ght_kernels.cuh -- bulk build and bulk find kernels for sm_103a.
+// ght_kernels.cuh -- bulk build kernels for sm_103a (the find kernel is in
+// ght_find.cuh, included here).
 //
 // Work distribution (a GB300 design, not the paper's): every lane owns one
-// key (or query) at a time, drawn from its warp's contiguous slice of the
-// input. A "tile" of G lanes reads one 128-byte bucket together, each lane
-// B/G pairs with 16-byte vector loads. In one round every tile member's
-// pending bucket is gathered back to back, so a warp keeps up to 32
-// independent bucket reads in flight; the owner then decides from ballots
-// over the tile (load = popcount of non-empty slots, key match), issues at
-// most one 64-bit CAS or exchange, and a lane whose key is done immediately
-// takes the next key of the warp's slice. The paper instead serialises a
-// tile over its lanes' keys, one bucket read in flight per tile (Sec. V-A).
+// key at a time, drawn from input chunks its warp claims. A "tile" of G
+// lanes reads one 128-byte bucket together, each lane B/G slots. In one
+// round every tile member's pending bucket is gathered back to back, so a
+// warp keeps up to 32 independent bucket reads in flight; the owner then
+// decides from ballots over the tile (load = popcount of non-empty slots),
+// issues at most one 64-bit CAS or exchange, and a lane whose key is done
+// immediately takes the next key. The paper instead serialises a tile over
+// its lanes' keys, one bucket read in flight per tile (Sec. V-A).
 #pragma once
 
 #include "ght_device.cuh"
+#include "ght_find.cuh"
 
 namespace ght {
-
-__device__ __forceinline__ unsigned lanemask_lt() {
-  unsigned m;
-  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-  return m;
-}
-
-// ----------------------------------------------------------------------------
-// Input stream of a warp's slice, read 32 items at a time with one coalesced
-// load and kept two chunks ahead of use, so refilling a lane never waits on
-// memory. Chunk x lives in register x of lane i (entry i).
-struct StreamQueue {
-  uint64_t base;  // slice index of entry 0 of chunk a (warp-uniform)
-  int head;       // next unused entry of chunk a (warp-uniform)
-  uint32_t a, b, c;
-};
-
-__device__ __forceinline__ uint32_t stream_load(const uint32_t *__restrict__ p, uint64_t i, uint64_t end) {
-  return i < end ? __ldg(p + i) : kEmptyKey;
-}
-
-__device__ __forceinline__ void stream_init(StreamQueue &q, const uint32_t *__restrict__ p, uint64_t beg,
-                                            uint64_t end, int lane) {
-  q.base = beg;
-  q.head = 0;
-  q.a = stream_load(p, beg + lane, end);
-  q.b = stream_load(p, beg + 32 + lane, end);
-  q.c = stream_load(p, beg + 64 + lane, end);
-}
-
-// Hand the next popc(need) entries to the lanes set in `need` (in lane
-// order); returns the entry's slice index (>= end when the slice is spent).
-__device__ __forceinline__ uint64_t stream_take(StreamQueue &q, const uint32_t *__restrict__ p, uint64_t end,
-                                                unsigned need, unsigned below, int lane, uint32_t &item) {
-  const int pos = q.head + __popc(need & below);
-  const uint32_t from_a = __shfl_sync(kFull, q.a, pos & 31);
-  const uint32_t from_b = __shfl_sync(kFull, q.b, pos & 31);
-  item = pos < 32 ? from_a : from_b;
-  const uint64_t at = q.base + (uint64_t)pos;
-  q.head += __popc(need);
-  if (q.head >= 32) {
-    q.head -= 32;
-    q.base += 32;
-    q.a = q.b;
-    q.b = q.c;
-    q.c = stream_load(p, q.base + 64 + lane, end);
-  }
-  return ((need >> lane) & 1u) ? at : ~0ull;
-}
-
-// ----------------------------------------------------------------------------
-// Bucketed find. BCHT stops at the first probed bucket with an empty slot
-// (Sec. V-B find; valid because keys are placed in hash order and buckets
-// never lose keys). P2BHT, IHT and the load-balanced BCHT read their
-// candidates in order until the key is found (Sec. V-C, V-D find).
-//
-// Each lane owns KPL queries (sets). With KPL = 2 the sets are staggered:
-// one set's bucket reads are in flight while the other set is evaluated.
-// Tile members report a hit (and its value) or an empty slot to the owner
-// through per-warp shared memory rather than one ballot per slot.
-template <int SCHEME, int B, int G, int KPL, bool COUNT, typename S = PairSlot>
-__global__ void __launch_bounds__(256)
-bucketed_find_kernel(TableView tv, const uint32_t *__restrict__ queries, uint32_t *__restrict__ out,
-                     uint64_t n, uint64_t per_warp) {
-  using T = typename S::T;
-  constexpr int PPL = B / G;
-  const T *slots = reinterpret_cast<const T *>(tv.slots);
-  constexpr bool kEarlyExit = (SCHEME == kBCHT);
-  static_assert(B % G == 0 && 32 % G == 0 && PPL >= 1 && (KPL == 1 || KPL == 2), "tile shape");
-  __shared__ uint32_t s_hit[8][32], s_emp[8][32], s_val[8][32];
-  const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  const int r = lane & (G - 1);
-  const int tbase = lane - r;
-  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint64_t beg = warp * per_warp;
-  if (beg >= n) return;  // whole warp
-  const uint64_t end = beg + per_warp < n ? beg + per_warp : n;
-  const unsigned below = lanemask_lt();
-
-  StreamQueue sq;
-  stream_init(sq, queries, beg, end, lane);
-  bool active[KPL];
-  uint32_t key[KPL], act[KPL];
-  uint64_t idx[KPL];
-  int probe[KPL];
-  T v[KPL][G][PPL];
-#pragma unroll
-  for (int s = 0; s < KPL; ++s) {
-    active[s] = false;
-    key[s] = kEmptyKey;
-    act[s] = 0u;
-    idx[s] = 0;
-    probe[s] = 0;
-  }
-  unsigned long long probes = 0, answered = 0;
-
-  for (;;) {
-#pragma unroll
-    for (int s = 0; s < KPL; ++s) {
-      // refill set s from the stream, then issue its bucket reads
-      const unsigned need = __ballot_sync(kFull, !active[s]);
-      if (need != 0u && sq.base + sq.head < end) {
-        uint32_t k;
-        const uint64_t at = stream_take(sq, queries, end, need, below, lane, k);
-        if (at < end) {
-          if (COUNT) answered++;
-          if (k == kEmptyKey) {
-            out[at] = S::missing();  // the sentinel is never a key
-          } else {
-            active[s] = true;
-            key[s] = k;
-            idx[s] = at;
-            probe[s] = 0;
-          }
-        }
-      }
-      act[s] = __ballot_sync(kFull, active[s]);
-      if (act[s] != 0u) {
-        const uint32_t myb = active[s] ? bucket_of(tv.hf, probe[s], key[s]) : 0u;
-#pragma unroll
-        for (int j = 0; j < G; ++j) {
-          const uint32_t bj = __shfl_sync(kFull, myb, tbase + j);
-          if ((act[s] >> (tbase + j)) & 1u) load_slots_ro<PPL>(slots + (uint64_t)bj * B, r, v[s][j]);
-        }
-      }
-      // evaluate the other set (or this one when KPL = 1)
-      const int e = (KPL == 1) ? s : (s + 1) % KPL;
-      if (act[e] != 0u) {
-        s_hit[wib][lane] = 0u;
-        if (kEarlyExit) s_emp[wib][lane] = 0u;
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < G; ++j) {
-          const int owner = tbase + j;
-          const uint32_t kj = __shfl_sync(kFull, key[e], owner);
-          if ((act[e] >> owner) & 1u) {
-#pragma unroll
-            for (int p = 0; p < PPL; ++p) {
-              const uint32_t sk = S::key(v[e][j][p]);
-              if (sk == kj) {
-                s_hit[wib][owner] = 1u;
-                s_val[wib][owner] = S::found(v[e][j][p]);
-              }
-              if (kEarlyExit && sk == kEmptyKey) s_emp[wib][owner] = 1u;
-            }
-          }
-        }
-        __syncwarp();
-        if ((act[e] >> lane) & 1u) {
-          if (COUNT) probes++;
-          bool finish = false;
-          uint32_t result = S::missing();
-          if (s_hit[wib][lane]) {
-            result = s_val[wib][lane];
-            finish = true;
-          } else if (kEarlyExit && s_emp[wib][lane]) {
-            finish = true;
-          } else if (++probe[e] >= tv.h) {
-            finish = true;
-          }
-          if (finish) {
-            out[idx[e]] = result;
-            active[e] = false;
-          }
-        }
-        act[e] = 0u;  // evaluated; the set's next reads are issued on its next refill
-      }
-    }
-    bool any = false;
-#pragma unroll
-    for (int s = 0; s < KPL; ++s) any |= active[s];
-    if (__ballot_sync(kFull, any) == 0u && sq.base + sq.head >= end) break;
-  }
-  if (COUNT) {
-    probes = warp_sum(probes);
-    answered = warp_sum(answered);
-    if (lane == 0) {
-      atomicAdd(&tv.ctrl->find_probes, probes);
-      atomicAdd(&tv.ctrl->find_queries, answered);
-    }
-  }
-}
 
 // ----------------------------------------------------------------------------
 // Key and value streams of a build, read like StreamQueue, 32 pairs at a
@@ -437,12 +255,12 @@ bucketed_insert_kernel(TableView tv, const uint32_t *__restrict__ keys,
       const unsigned act = __ballot_sync(kFull, active[s]);
       if (act == 0u) continue;
 
-      // -- gather one bucket per active lane of the tile
-      T v[G][PPL];
+      // -- gather the keys of one bucket per active lane of the tile
+      uint32_t v[G][PPL];
 #pragma unroll
       for (int j = 0; j < G; ++j) {
         const uint32_t bj = __shfl_sync(kFull, cur[s], tbase + j);
-        if ((act >> (tbase + j)) & 1u) load_slots_rw<PPL>(slots + (uint64_t)bj * B, r, v[j]);
+        if ((act >> (tbase + j)) & 1u) load_keys_rw<PPL>(slots + (uint64_t)bj * B, r, v[j]);
       }
       // owner learns how many slots are empty and where one of them is
       int my_empty = 0, my_slot = -1;
@@ -452,7 +270,7 @@ bucketed_insert_kernel(TableView tv, const uint32_t *__restrict__ keys,
         int cnt = 0, slot = -1;
 #pragma unroll
         for (int p = 0; p < PPL; ++p) {
-          const unsigned em = __ballot_sync(kFull, aj && S::key(v[j][p]) == kEmptyKey) & tmask;
+          const unsigned em = __ballot_sync(kFull, aj && v[j][p] == kEmptyKey) & tmask;
           cnt += __popc(em);
           if (slot < 0 && em) slot = (__ffs(em) - 1 - tbase) * PPL + p;
         }
@@ -570,6 +388,124 @@ bucketed_insert_kernel(TableView tv, const uint32_t *__restrict__ keys,
       atomicAdd(&tv.ctrl->insert_evictions, evictions);
       atomicMax(&tv.ctrl->longest_chain, longest);
     }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Ranked first-choice placement: phase 1 of a two-phase BCHT build.
+//
+// Sequential BCHT (Sec. III-A) may insert the keys in any order. Take the
+// order in which, first, every key that arrives at its first-choice bucket
+// H_0 while that bucket still has room is inserted, and then all other keys.
+// In the first part no bucket is ever full, so each insert is one probe that
+// takes the next free slot of H_0 -- and the slot is known without reading
+// the bucket: it is the key's arrival rank at H_0. This kernel counts
+// arrivals per bucket with one atomic increment on a per-bucket counter
+// (4 bytes per bucket, small enough to stay in L2), stores a key of rank
+// r < B straight into slot r, and appends keys of rank >= B to an overflow
+// list; the overflow keys are then inserted by the BCHT insert kernel, whose
+// first probe finds H_0 full and evicts as Sec. V-B prescribes. The table must
+// be filled with empty slots and the counters zeroed before the launch.
+//
+// Blocks claim input tiles from a cursor in the control block (zeroed by the
+// fill), so all blocks advance through the input together: on pairs grouped
+// by first-choice bucket range, the stores and counter increments in flight
+// then stay inside a few MB of the table, whose lines fill up in L2 and
+// leave it once, whole. Overflow keys are staged per block in shared memory
+// and appended to the list one block tile at a time with a single global
+// reservation on the control block's overflow count; entries past `cap` are
+// not written (the caller sees the count exceed cap and builds the ordinary
+// way).
+constexpr int kPlacePerThread = 4;
+constexpr int kPlaceTile = 256 * kPlacePerThread;
+
+template <int B, bool COUNT, typename S = PairSlot>
+__global__ void __launch_bounds__(256)
+rank_place_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint32_t *__restrict__ values,
+                  uint64_t n, uint32_t *__restrict__ counters, uint32_t *__restrict__ ovf_k,
+                  uint32_t *__restrict__ ovf_v, uint64_t cap) {
+  using T = typename S::T;
+  T *slots = reinterpret_cast<T *>(tv.slots);
+  unsigned long long *ovf_count = &tv.ctrl->reserved[0];
+  unsigned long long *tile_cursor = &tv.ctrl->reserved[1];
+  __shared__ uint32_t s_k[2 * kPlaceTile], s_v[2 * kPlaceTile];
+  __shared__ uint32_t s_n;
+  __shared__ unsigned long long s_base, s_tile[2];
+  const int lane = threadIdx.x & 31;
+  const unsigned below = lanemask_lt();
+  if (threadIdx.x == 0) {
+    s_n = 0u;
+    s_tile[0] = atomicAdd(tile_cursor, (unsigned long long)kPlaceTile);
+  }
+  __syncthreads();
+  unsigned long long placed = 0;
+  // Tile i is s_tile[i & 1]; thread 0 claims tile i + 1 into the other entry
+  // while tile i is processed (that entry was last read before the barrier
+  // that ended tile i - 1). s_n is bumped while a tile is processed, read
+  // after barrier (A) and reset inside a flush.
+  for (int it = 0;; it ^= 1) {
+    const uint64_t t0 = s_tile[it];
+    if (t0 >= n) break;  // block-uniform
+    if (threadIdx.x == 0) s_tile[it ^ 1] = atomicAdd(tile_cursor, (unsigned long long)kPlaceTile);
+    uint32_t k[kPlacePerThread], v[kPlacePerThread], b[kPlacePerThread], r[kPlacePerThread];
+    bool ok[kPlacePerThread];
+#pragma unroll
+    for (int u = 0; u < kPlacePerThread; ++u) {
+      const uint64_t i = t0 + (uint64_t)u * blockDim.x + threadIdx.x;  // coalesced
+      ok[u] = i < n;
+      k[u] = ok[u] ? __ldg(keys + i) : kEmptyKey;
+      v[u] = ok[u] ? __ldg(values + i) : 0u;
+      if (ok[u] && k[u] == kEmptyKey) {
+        atomicOr(&tv.ctrl->status, kStatusSentinel);
+        ok[u] = false;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kPlacePerThread; ++u) {
+      b[u] = ok[u] ? bucket_of(tv.hf, 0, k[u]) : 0u;
+      r[u] = ok[u] ? atomicAdd(counters + b[u], 1u) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kPlacePerThread; ++u) {
+      const bool fits = ok[u] && r[u] < (uint32_t)B;
+      if (fits) {
+        slots[(uint64_t)b[u] * B + r[u]] = S::make(k[u], v[u]);
+        if (COUNT) placed++;
+      }
+      // overflow: one shared reservation per warp (< 2 * kPlaceTile entries
+      // are staged: they are flushed below once above one tile)
+      const unsigned over = __ballot_sync(kFull, ok[u] && !fits);
+      if (over) {
+        uint32_t at = 0;
+        if (lane == 0) at = atomicAdd(&s_n, (uint32_t)__popc(over));
+        at = __shfl_sync(kFull, at, 0) + __popc(over & below);
+        if ((over >> lane) & 1u) {
+          s_k[at] = k[u];
+          s_v[at] = v[u];
+        }
+      }
+    }
+    __syncthreads();  // (A)
+    const uint32_t staged = s_n;
+    const bool last = s_tile[it ^ 1] >= n;  // no further tile for this block
+    if (staged > (uint32_t)kPlaceTile || (last && staged > 0u)) {
+      if (threadIdx.x == 0) s_base = atomicAdd(ovf_count, (unsigned long long)staged);
+      __syncthreads();
+      const unsigned long long base = s_base;
+      for (uint32_t i = threadIdx.x; i < staged; i += blockDim.x) {
+        if (base + i < cap) {
+          ovf_k[base + i] = s_k[i];
+          ovf_v[base + i] = s_v[i];
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) s_n = 0u;
+    }
+    __syncthreads();
+  }
+  if (COUNT) {
+    placed = warp_sum(placed);
+    if ((threadIdx.x & 31) == 0 && placed) atomicAdd(&tv.ctrl->insert_probes, placed);
   }
 }
 

@@ -39,6 +39,25 @@ static cudaError_t find_shape(const TableView &tv, const uint32_t *q, uint32_t *
   return o.keys_per_lane == 1 ? find_kpl<B, G, 1>(tv, q, out, n, o, s) : find_kpl<B, G, 2>(tv, q, out, n, o, s);
 }
 
+template <int B>
+static cudaError_t place_b(const TableView &tv, const uint32_t *k, const uint32_t *v, uint64_t n,
+                          const PlaceBuffers &pb, bool count, cudaStream_t s) {
+  auto kern = count ? rank_place_kernel<B, true> : rank_place_kernel<B, false>;
+  int blocks = 0;
+  cudaError_t e = grid_for(kern, (n + kPlacePerThread - 1) / kPlacePerThread, 0, &blocks);
+  if (e != cudaSuccess) return e;
+  kern<<<blocks, kThreads, 0, s>>>(tv, k, v, n, pb.counters, pb.ovf_k, pb.ovf_v, pb.cap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_place_bcht(int B, const TableView &tv, const uint32_t *k, const uint32_t *v, uint64_t n,
+                              const PlaceBuffers &pb, bool count, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  if (B == 16) return place_b<16>(tv, k, v, n, pb, count, s);
+  if (B == 32) return place_b<32>(tv, k, v, n, pb, count, s);
+  return cudaErrorInvalidValue;
+}
+
 bool bcht_shape_supported(int B, int G) {
   return (B == 16 && (G == 4 || G == 8 || G == 16)) || (B == 32 && (G == 8 || G == 16));
 }

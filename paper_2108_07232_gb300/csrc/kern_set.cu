@@ -33,6 +33,18 @@ static cudaError_t set_find(const TableView &tv, const uint32_t *q, uint32_t *ou
 
 bool set_shape_supported(int B, int G) { return B == 32 && G == 8; }
 
+cudaError_t launch_place_set(const TableView &tv, const uint32_t *k, uint64_t n, const PlaceBuffers &pb, bool count,
+                             cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  auto kern = count ? rank_place_kernel<32, true, KeySlot> : rank_place_kernel<32, false, KeySlot>;
+  int blocks = 0;
+  cudaError_t e = grid_for(kern, (n + kPlacePerThread - 1) / kPlacePerThread, 0, &blocks);
+  if (e != cudaSuccess) return e;
+  // a set has no values: the key array stands in for them and is ignored
+  kern<<<blocks, kThreads, 0, s>>>(tv, k, k, n, pb.counters, pb.ovf_k, pb.ovf_v, pb.cap);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_insert_set(const TableView &tv, const uint32_t *k, const uint32_t *v, uint64_t n,
                               const LaunchOpts &o, cudaStream_t s) {
   if (o.tile_lanes != 8) return cudaErrorInvalidValue;

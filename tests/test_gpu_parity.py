@@ -329,3 +329,30 @@ def test_full_size_bcht_sampled_parity(G):
         for jj in range(j):  # early-exit invariant: earlier candidates are full
             row = slots[cands[jj] * 16:(cands[jj] + 1) * 16]
             assert int((row == -1).sum()) == 0
+
+
+@pytest.mark.parametrize("b,lanes,lf", [(16, 16, 0.99), (16, 8, 0.95), (16, 4, 0.9), (32, 8, 0.99),
+                                        (32, 16, 0.97)])
+def test_bcht_build_shapes_at_a_million_keys(G, b, lanes, lf):
+    """Every BCHT insert shape (one key per lane), at 2^20 + 19 keys -- many
+    rounds per lane, heavy contention on each bucket -- builds a valid table
+    whose finds equal the definitional lookup and reads as many buckets per
+    insert as the sequential oracle."""
+    n = (1 << 20) + 19
+    t, keys, vals = build_table(G, O.BCHT, n, lf, seed=21, bucket_size=b, build_tile_lanes=lanes,
+                                build_keys_per_lane=1)
+    st = t.stats()
+    assert st["built"] == 1 and st["n_stored"] == n
+    T = oracle_view(st, O.BCHT, n, lf)
+    slots = t.export()
+    ok, msg = T.validate(keys, vals, slots=slots)
+    assert ok, msg
+    q = W.make_queries(keys, n, 0.5, seed=5)
+    t.reset_counters()
+    got = t.find(q.cuda()).cpu()
+    assert (O._u32(got) == O.lookup(keys, vals, q)).all()
+    assert t.stats()["find_probes"] == T.find(q, slots=slots)[2]
+    S = oracle_view(st, O.BCHT, n, lf)
+    assert S.build(keys, vals) == 1
+    gpu, cpu = st["insert_probes"] / n, S.stats.probes / n
+    assert abs(gpu - cpu) <= 0.05, (gpu, cpu)

@@ -1,0 +1,153 @@
+"""The two-phase BCHT build (ranked first-choice placement, then the cuckoo
+insert of the overflow) against the oracle, called through the C ABI.
+
+Sequential BCHT (Sec. III-A) may take the keys in any order; the two-phase
+build is the order in which the keys that find room in their first-choice
+bucket come first. So it must build tables that pass every invariant of the
+oracle's validator, whose finds equal the definitional lookup bit for bit, and
+whose insert probe average (each placed key one probe, plus the cuckoo
+insert's reads) matches the sequential oracle's.
+"""
+
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_07232_gb300 import build
+    build.build()
+    import paper_2108_07232_gb300 as G
+    return G
+
+
+def _check(t, scheme, keys, vals, n, lf, b):
+    st = t.stats()
+    assert st["built"] == 1 and st["n_stored"] == n
+    T = O.Table(scheme, n, lf, b=b, m=st["num_buckets"])
+    T.set_constants(st["hash_a"], st["hash_c"])
+    slots = t.export()
+    ok, msg = T.validate(keys, vals, slots=slots)
+    assert ok, msg
+    q = W.make_queries(keys, n + 11, 0.5, seed=4)
+    t.reset_counters()
+    got = O._u32(t.find(q.cuda()).cpu())
+    assert (got == O.lookup(keys, vals, q)).all()
+    assert t.stats()["find_probes"] == T.find(q, slots=slots)[2]
+    return st
+
+
+@pytest.mark.parametrize("b,lf", [(16, 0.99), (16, 0.9), (32, 0.99)])
+@pytest.mark.parametrize("group,ranked", [(1, 0), (1, -1), (-1, 1), (-1, -1)])
+def test_two_phase_and_cuckoo_only_builds(G, b, lf, group, ranked):
+    """Grouped or not, placed by rank first or not: the same table
+    invariants, finds and probe counts. (group_build = 1 with ranked_build at
+    its default places by rank.)"""
+    n = (1 << 20) + 7
+    keys, vals = W.make_keys(n, 91), W.make_values(n, 91)
+    t = G.HashTable("bcht", n, lf, seed=17, count_probes=1, bucket_size=b, group_build=group,
+                    ranked_build=ranked)
+    t.build(keys.cuda(), vals.cuda())
+    st = _check(t, O.BCHT, keys, vals, n, lf, b)
+    want_ranked = ranked > 0 or (ranked == 0 and group > 0)
+    assert st["last_build_ranked"] == int(want_ranked)
+    assert st["last_build_grouped"] == int(group > 0)
+    if want_ranked:
+        assert st["last_place_ms"] >= 0.0
+        assert (st["last_group_ms"] >= 0.0) == (group > 0)
+        # keys beyond b arrivals at their first-choice bucket: a few per cent
+        # at these load factors (about 9.5 % at 0.99 with b = 16)
+        assert 0 < st["place_overflow"] < 0.15 * n
+    S = O.Table(O.BCHT, n, lf, b=b, m=st["num_buckets"])
+    S.set_constants(st["hash_a"], st["hash_c"])
+    assert S.build(keys, vals) == 1
+    gpu, cpu = st["insert_probes"] / n, S.stats.probes / n
+    assert abs(gpu - cpu) <= 0.05, (gpu, cpu)
+
+
+@pytest.mark.parametrize("lf", [0.9, 0.99])
+@pytest.mark.parametrize("group", [1, -1])
+def test_two_phase_keys_only_set(G, lf, group):
+    n = (1 << 18) + 5
+    keys = W.make_keys(n, 92)
+    zeros = torch.zeros(n, dtype=torch.int32)
+    t = G.HashTable("bcht_set", n, lf, seed=2, group_build=group, ranked_build=1)
+    t.build(keys.cuda())  # no values: the grouping carries the keys in their place
+    st = t.stats()
+    assert st["built"] == 1 and st["last_build_ranked"] == 1
+    assert st["last_build_grouped"] == int(group > 0)
+    T = O.Table(O.BCHT, n, lf, b=32, m=st["num_buckets"])
+    T.set_constants(st["hash_a"], st["hash_c"])
+    s32 = t.export()
+    pairs = np.where(s32 == O.EMPTY, np.uint64(O.EMPTY_PAIR), s32.astype(np.uint64))
+    ok, msg = T.validate(keys, zeros, slots=pairs)
+    assert ok, msg
+    q = W.make_queries(keys, n, 0.5, seed=3)
+    got = O._u32(t.find(q.cuda()).cpu())
+    assert (got == (O.lookup(keys, zeros, q) != O.EMPTY).astype(np.uint32)).all()
+
+
+def test_two_phase_from_host_buffers(G):
+    n = (1 << 23) + (1 << 20) + 3  # two host-to-device chunks, the second ragged
+    keys, vals = W.make_keys(n, 93), W.make_values(n, 93)
+    t = G.HashTable("bcht", n, 0.97, seed=5, count_probes=1, ranked_build=1)
+    t.build(keys, vals)  # CPU tensors: ght_build_host, placement overlapped with the copies
+    st = _check(t, O.BCHT, keys, vals, n, 0.97, 16)
+    assert st["last_build_ranked"] == 1
+
+
+def test_overflow_beyond_the_list_falls_back_to_the_cuckoo_insert(G):
+    """6,000 of 20,000 keys share one first-choice bucket under the first
+    attempt's constants: far more overflow than the list holds, so that
+    attempt inserts every key with the cuckoo insert (or fails and the next
+    attempt, with fresh constants, places them by rank)."""
+    n, lf, seed = 20000, 0.9, 29
+    m = O.num_buckets(n, lf, 16)
+    a, c = O.derive_constants(seed, 0, 3)
+    cand = np.arange(1, 1 << 24, dtype=np.uint64)
+    h0 = ((np.uint64(a[0]) * cand + np.uint64(c[0])) % np.uint64(O.PRIME)) % np.uint64(m)
+    same = cand[h0 == h0[0]][:6000].astype(np.uint32)
+    assert same.size == 6000
+    rest = W.make_keys(3 * n, 94).numpy().view(np.uint32)
+    rest = rest[~np.isin(rest, same)][: n - same.size]
+    keys_np = np.concatenate([same, rest])
+    assert np.unique(keys_np).size == n
+    keys = torch.from_numpy(keys_np.view(np.int32).copy())
+    vals = W.make_values(n, 94)
+    t = G.HashTable("bcht", n, lf, seed=seed, count_probes=1, ranked_build=1)
+    t.build(keys.cuda(), vals.cuda())
+    st = _check(t, O.BCHT, keys, vals, n, lf, 16)
+    assert st["attempts"] > 1 or (st["last_build_ranked"] == 0 and st["place_overflow"] > n // 4 + 1024)
+
+
+def test_no_scratch_means_cuckoo_insert_of_every_key(G):
+    """A table on caller storage with no scratch set builds with the cuckoo
+    insert alone (the ranked placement needs its counters and list)."""
+    n, lf = 50000, 0.95
+    keys, vals = W.make_keys(n, 95), W.make_values(n, 95)
+    nbytes = G.ght_table_bytes(G.BCHT, n, lf, {"ranked_build": 1})
+    store = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    base = (store.data_ptr() + 255) & ~255
+    h = G.ght_create_ex(G.BCHT, n, lf, 3, {"ranked_build": 1}, base, nbytes)
+    try:
+        assert G.ght_build_scratch_bytes(h, n) > 0
+        dk, dv = keys.cuda(), vals.cuda()
+        G.ght_build(h, dk, dv, n)
+        st = G.ght_stats(h).as_dict()
+        assert st["built"] == 1 and st["last_build_ranked"] == 0
+        q = W.make_queries(keys, n, 0.5, seed=6).cuda()
+        out = torch.empty_like(q)
+        G.ght_find(h, q, out, n)
+        torch.cuda.synchronize()
+        assert (O._u32(out.cpu()) == O.lookup(keys, vals, q.cpu())).all()
+    finally:
+        G.ght_destroy(h)
