@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--tile-lanes", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--build-tile-lanes", type=int, default=0)
+    ap.add_argument("--keys-per-lane", type=int, default=0, help="find: query sets in flight per lane")
     ap.add_argument("--group-build", type=int, default=0, choices=[-1, 0, 1],
                     help="1: group the pairs by first-choice bucket range before the build")
     ap.add_argument("--ranked-build", type=int, default=0, choices=[-1, 0],
@@ -150,7 +151,8 @@ class ClockSampler:
 # from one ncu capture (profiles/bcht_find_n2e28_traffic.md). It describes the
 # kernel source it was captured from, identified by a hash of the find
 # kernel's headers; after any change to them the traffic is reported as null.
-FIND_TRAFFIC = {"bytes_per_launch": 60374900032, "source_sha256_16": "d54d51a32b04541d"}
+FIND_TRAFFIC = {"bytes_per_launch": 60382687808, "source_sha256_16": "c5a43adc96f0a9f3",
+               "kernel": "bucketed_find_kernel"}
 
 
 def kernel_source_hash() -> str:
@@ -303,6 +305,8 @@ def run_ours(args, world, rank, local):
         cfg["ranked_build"] = args.ranked_build
     if args.group_build:
         cfg["group_build"] = args.group_build
+    if args.keys_per_lane:
+        cfg["keys_per_lane"] = args.keys_per_lane
     tables = {lf: G.HashTable("bcht", n, lf, seed=seed, **cfg) for lf in LFS}
     torch.cuda.synchronize()
 
@@ -415,7 +419,7 @@ def run_ours(args, world, rank, local):
     dom_name = max(per_func, key=lambda f: per_func[f]["ms_per_step"])
     dom = per_func[dom_name]
     traffic = None
-    if (dom_name == "bucketed_find_kernel" and args.log2n == 28
+    if (dom_name == FIND_TRAFFIC.get("kernel", "bucketed_find_kernel") and args.log2n == 28
             and kernel_source_hash() == FIND_TRAFFIC["source_sha256_16"]):
         traffic = FIND_TRAFFIC["bytes_per_launch"]
     alg_per_launch = sum(kernels[k]["bytes_per_key"] * n for k in funcs[dom_name]) / len(funcs[dom_name])
