@@ -434,3 +434,46 @@ def test_chain_bound_is_exact(golden_dir):
         T.params.max_chain = bound
         assert T.insert(7, 1007, rng_state=99) == ok
         assert (T.stats.probes, T.stats.evictions) == (probes, evictions)
+
+
+@pytest.mark.parametrize("lf", [0.9, 0.99])
+def test_two_phase_order_is_a_bcht_insertion_order(lf):
+    """The two-phase GPU build is sequential BCHT (Sec. III-A) with the keys
+    permuted: first every key that reaches its first-choice bucket H_0 while
+    fewer than b keys have (arrival rank < b), then the rest, each part in
+    input order. In the first part no bucket is full, so each insert is one
+    probe with no eviction and lands in slot `rank` of H_0; the whole order
+    builds a valid table whose finds equal the definitional lookup, with an
+    insert probe average close to input order's."""
+    n = 1 << 16
+    keys, vals = W.make_keys(n, 17), W.make_values(n, 17)
+    k = O._u32(keys).astype(np.uint64)
+    T = O.Table(O.BCHT, n, lf, seed=5)
+    a, c = T.constants()
+    h0 = ((np.uint64(a[0]) * k + np.uint64(c[0])) % np.uint64(O.PRIME)) % np.uint64(T.m)
+    # arrival rank of each key at its H_0, in input order
+    order = np.argsort(h0, kind="stable")
+    sorted_h0 = h0[order]
+    first = np.searchsorted(sorted_h0, sorted_h0, side="left")
+    rank = np.empty(n, dtype=np.int64)
+    rank[order] = np.arange(n) - first
+    placed = rank < T.b
+    assert 0.03 * n < (~placed).sum() < 0.15 * n  # the overflow of the first part
+    # part one alone: one probe per key, no eviction, slot = arrival rank
+    P = O.Table(O.BCHT, n, lf, seed=5)
+    assert P.build(keys[placed], vals[placed]) == 1
+    assert P.stats.probes == placed.sum() and P.stats.evictions == 0
+    slots = P.slots.reshape(P.m, P.b)
+    kp = O._u32(keys)[placed]
+    assert (slots[h0[placed].astype(np.int64), rank[placed]] & np.uint64(0xFFFFFFFF) == kp).all()
+    # the whole permuted order
+    perm = np.concatenate([np.flatnonzero(placed), np.flatnonzero(~placed)])
+    R = O.Table(O.BCHT, n, lf, seed=5)
+    assert R.build(keys[perm], vals[perm]) == 1
+    ok, msg = R.validate(keys, vals)
+    assert ok, msg
+    q = W.make_queries(keys, n, 0.5, seed=3)
+    assert (R.find(q)[0] == O.lookup(keys, vals, q)).all()
+    S = O.Table(O.BCHT, n, lf, seed=5)
+    assert S.build(keys, vals) == 1
+    assert abs(R.stats.probes - S.stats.probes) / n < 0.03, (R.stats.probes / n, S.stats.probes / n)
