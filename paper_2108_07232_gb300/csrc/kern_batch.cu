@@ -92,6 +92,78 @@ __device__ __forceinline__ void bq_init(BatchQueue &q, const uint32_t *__restric
   bq_load<PAIRS>(q.kc, q.vc, q.tc, keys, vals, beg + 64, end, bv, offs, lane);
 }
 
+// Key/value stream of the batched insert: 32-pair chunks claimed from the
+// batch's work cursor (runs of kClaimChunks chunks per claim, as in the
+// single-table insert), each with the table of its first pair, kept two
+// chunks ahead of use.
+struct BatchClaimQueue {
+  uint64_t ba, bb, bc;  // index of entry 0 of chunks a, b, c (warp-uniform)
+  uint64_t claim_next;  // next chunk of the warp's current claim
+  uint32_t claim_left;  // chunks left in that claim
+  int head;             // next unused entry of chunk a
+  uint32_t ta, tb, tc;  // table of each chunk's first pair
+  uint32_t ka, kb, kc, va, vb, vc;
+};
+
+__device__ __forceinline__ uint64_t bc_claim(BatchClaimQueue &q, Ctrl *ctrl, uint64_t lo, int lane) {
+  if (q.claim_left == 0) {
+    unsigned long long x = 0ull;
+    if (lane == 0) x = atomicAdd(&ctrl->work_cursor, 32ull * kClaimChunks);
+    q.claim_next = lo + __shfl_sync(kFull, x, 0);
+    q.claim_left = kClaimChunks;
+  }
+  const uint64_t at = q.claim_next;
+  q.claim_next += 32;
+  q.claim_left--;
+  return at;
+}
+
+__device__ __forceinline__ void bc_init(BatchClaimQueue &q, const uint32_t *__restrict__ keys,
+                                        const uint32_t *__restrict__ vals, uint64_t lo, uint64_t hi,
+                                        const BatchView &bv, const uint64_t *__restrict__ offs, int lane) {
+  q.claim_next = 0;
+  q.claim_left = 0;
+  q.head = 0;
+  q.ba = bc_claim(q, bv.ctrl, lo, lane);
+  q.bb = bc_claim(q, bv.ctrl, lo, lane);
+  q.bc = bc_claim(q, bv.ctrl, lo, lane);
+  bq_load<true>(q.ka, q.va, q.ta, keys, vals, q.ba, hi, bv, offs, lane);
+  bq_load<true>(q.kb, q.vb, q.tb, keys, vals, q.bb, hi, bv, offs, lane);
+  bq_load<true>(q.kc, q.vc, q.tc, keys, vals, q.bc, hi, bv, offs, lane);
+}
+
+// Hand the next popc(need) pairs to the lanes in `need`; returns the pair's
+// index (~0 for lanes without one) and its table.
+__device__ __forceinline__ uint64_t bc_take(BatchClaimQueue &q, const uint32_t *__restrict__ keys,
+                                            const uint32_t *__restrict__ vals, uint64_t lo, uint64_t hi,
+                                            const BatchView &bv, const uint64_t *__restrict__ offs, unsigned need,
+                                            unsigned below, int lane, uint32_t &key, uint32_t &val, uint32_t &table) {
+  const int pos = q.head + __popc(need & below);
+  const uint32_t ka = __shfl_sync(kFull, q.ka, pos & 31), kb = __shfl_sync(kFull, q.kb, pos & 31);
+  const uint32_t va = __shfl_sync(kFull, q.va, pos & 31), vb = __shfl_sync(kFull, q.vb, pos & 31);
+  key = pos < 32 ? ka : kb;
+  val = pos < 32 ? va : vb;
+  const uint64_t at = pos < 32 ? q.ba + (uint64_t)pos : q.bb + (uint64_t)(pos - 32);
+  table = pos < 32 ? q.ta : q.tb;
+  q.head += __popc(need);
+  if (q.head >= 32) {
+    q.head -= 32;
+    q.ba = q.bb;
+    q.bb = q.bc;
+    q.bc = bc_claim(q, bv.ctrl, lo, lane);
+    q.ka = q.kb;
+    q.kb = q.kc;
+    q.va = q.vb;
+    q.vb = q.vc;
+    q.ta = q.tb;
+    q.tb = q.tc;
+    bq_load<true>(q.kc, q.vc, q.tc, keys, vals, q.bc, hi, bv, offs, lane);
+  }
+  if (!((need >> lane) & 1u) || at >= hi) return ~0ull;
+  table = advance_table(offs, table, bv.t_hi, at);
+  return at;
+}
+
 // ----------------------------------------------------------------------------
 // Fill the slots of tables [t_lo, t_hi) and clear their status words.
 __global__ void __launch_bounds__(256) batch_fill_kernel(BatchView bv, uint4 *__restrict__ slots16, uint64_t n16) {
@@ -100,15 +172,16 @@ __global__ void __launch_bounds__(256) batch_fill_kernel(BatchView bv, uint4 *__
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) slots16[i] = e;
   for (uint64_t t = bv.t_lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < bv.t_hi; t += stride)
     bv.tables[t].status = 0u;
+  if (blockIdx.x == 0 && threadIdx.x == 0) bv.ctrl->work_cursor = 0ull;  // the insert's claims start at zero
 }
 
 // ----------------------------------------------------------------------------
 // BCHT bulk build of every table in [t_lo, t_hi) (Sec. III-A, V-B), with the
-// turn structure of the single-table insert kernel.
+// turn structure, chunk claims (the batch's work cursor, zeroed by the fill),
+// key-word gathers and register bound of the single-table insert kernel.
 template <int G, int KPL, bool COUNT>
-__global__ void __launch_bounds__(256)
-batch_insert_kernel(BatchView bv, const uint32_t *__restrict__ keys, const uint32_t *__restrict__ values,
-                    uint64_t per_warp) {
+__global__ void __launch_bounds__(256, insert_min_blocks<16, G, KPL, COUNT>())
+batch_insert_kernel(BatchView bv, const uint32_t *__restrict__ keys, const uint32_t *__restrict__ values) {
   constexpr int B = 16;
   constexpr int PPL = B / G;
   static_assert(B % G == 0 && 32 % G == 0 && (KPL == 1 || KPL == 2), "tile shape");
@@ -119,15 +192,12 @@ batch_insert_kernel(BatchView bv, const uint32_t *__restrict__ keys, const uint3
   const unsigned tmask = (G == 32 ? kFull : ((1u << G) - 1u)) << tbase;
   const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t lo = __ldg(offs + bv.t_lo), hi = __ldg(offs + bv.t_hi);
-  const uint64_t beg = lo + (gtid >> 5) * per_warp;
-  if (beg >= hi) return;  // whole warp
-  const uint64_t end = beg + per_warp < hi ? beg + per_warp : hi;
   const unsigned below = lanemask_lt();
   const int h = bv.h;
 
   uint32_t rng = lane_seed(bv.rng_seed, gtid);
-  BatchQueue q;
-  bq_init<true>(q, keys, values, beg, end, bv, offs, lane);
+  BatchClaimQueue q;
+  bc_init(q, keys, values, lo, hi, bv, offs, lane);
   bool active[KPL], retrying[KPL];
   uint64_t pair[KPL], old[KPL];
   uint32_t cur[KPL], chain[KPL], steps[KPL], tab[KPL];
@@ -172,9 +242,9 @@ batch_insert_kernel(BatchView bv, const uint32_t *__restrict__ keys, const uint3
       op[s] = 0;
       // -- refill
       const unsigned need = __ballot_sync(kFull, !active[s]);
-      if (need != 0u && q.base + q.head < end) {
+      if (need != 0u && q.ba + q.head < hi) {
         uint32_t k, val, tb;
-        const uint64_t at = bq_take<true>(q, keys, values, end, bv, offs, need, below, lane, k, val, tb);
+        const uint64_t at = bc_take(q, keys, values, lo, hi, bv, offs, need, below, lane, k, val, tb);
         if (at != ~0ull) {
           if (k == kEmptyKey) {
             atomicOr(&bv.tables[tb].status, kStatusSentinel);
@@ -192,11 +262,12 @@ batch_insert_kernel(BatchView bv, const uint32_t *__restrict__ keys, const uint3
       if (act == 0u) continue;
       // -- gather: each member's bucket address (its own table)
       uint64_t *myb = active[s] ? bv.tables[tab[s]].slots + (uint64_t)cur[s] * B : nullptr;
-      uint64_t v[G][PPL];
+      uint32_t v[G][PPL];  // key words only: emptiness is all an insert reads
 #pragma unroll
       for (int j = 0; j < G; ++j) {
         uint64_t *bj = reinterpret_cast<uint64_t *>(__shfl_sync(kFull, reinterpret_cast<uintptr_t>(myb), tbase + j));
-        if ((act >> (tbase + j)) & 1u) load_part_rw<PPL>(bj, r, v[j]);
+        if ((act >> (tbase + j)) & 1u)
+          load_keys_rw<PPL>(reinterpret_cast<const unsigned long long *>(bj), r, v[j]);
       }
       int my_empty = 0, my_slot = -1;
 #pragma unroll
@@ -205,7 +276,7 @@ batch_insert_kernel(BatchView bv, const uint32_t *__restrict__ keys, const uint3
         int cnt = 0, slot = -1;
 #pragma unroll
         for (int p = 0; p < PPL; ++p) {
-          const unsigned em = __ballot_sync(kFull, aj && pair_key(v[j][p]) == kEmptyKey) & tmask;
+          const unsigned em = __ballot_sync(kFull, aj && v[j][p] == kEmptyKey) & tmask;
           cnt += __popc(em);
           if (slot < 0 && em) slot = (__ffs(em) - 1 - tbase) * PPL + p;
         }
@@ -241,7 +312,7 @@ batch_insert_kernel(BatchView bv, const uint32_t *__restrict__ keys, const uint3
     bool any = false;
 #pragma unroll
     for (int s = 0; s < KPL; ++s) any |= active[s];
-    if (__ballot_sync(kFull, any) == 0u && q.base + q.head >= end) break;
+    if (__ballot_sync(kFull, any) == 0u && q.ba + q.head >= hi) break;
   }
   if (COUNT) {
     probes = warp_sum(probes);
@@ -406,10 +477,9 @@ static cudaError_t insert_cfg(const BatchView &bv, const uint32_t *k, const uint
                               const LaunchOpts &o, cudaStream_t s) {
   auto kern = o.count ? batch_insert_kernel<G, KPL, true> : batch_insert_kernel<G, KPL, false>;
   int blocks = 0;
-  uint64_t pw = 0;
-  cudaError_t e = launch_sliced(kern, items, o.blocks_per_sm, s, &blocks, &pw);
+  cudaError_t e = grid_for(kern, items, o.blocks_per_sm, &blocks);
   if (e != cudaSuccess) return e;
-  kern<<<blocks, kThreads, 0, s>>>(bv, k, v, pw);
+  kern<<<blocks, kThreads, 0, s>>>(bv, k, v);  // claims from bv.ctrl->work_cursor, zeroed by the fill
   return cudaGetLastError();
 }
 
