@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--ranked-build", type=int, default=0, choices=[-1, 0],
                     help="BCHT build: 0 two-phase (ranked first-choice placement, then cuckoo insert), "
                          "-1 cuckoo insert of every key")
-    ap.add_argument("--workload", choices=["hbm", "batched", "served", "sweep", "success"], default="hbm",
+    ap.add_argument("--workload", choices=["hbm", "batched", "served", "sweep", "success", "sizes"], default="hbm",
                     help="hbm: 2^28-key BCHT tables (default); batched: 512 uneven tables in one graph "
                          "launch; served: a table pool under Poisson request arrivals")
     ap.add_argument("--served-seconds", type=float, default=1.0, help="served: length of the arrival trace")
@@ -680,6 +680,41 @@ def _time_ms(fn, reps=5):
     return statistics.median(ts)
 
 
+def measure_table(scheme, n, lf, fracs, seed, dev, **cfg):
+    """Build and find throughput (Gkeys/s, CUDA events, median of reps) and probe
+    counts of one table configuration on synthetic keys."""
+    import torch
+
+    import paper_2108_07232_gb300 as G
+    import workloads as W
+
+    keys, vals = W.make_keys(n, seed, device=dev), W.make_values(n, seed, device=dev)
+    negs = W.make_negatives(n, n, seed, device=dev)
+    qs = {f: W.make_queries(keys, n, f, seed, negs) for f in fracs}
+    out = torch.empty_like(keys)
+    t = G.HashTable(scheme, n, lf, seed=seed, max_attempts=3, **cfg)
+    try:
+        t.build(keys, vals)
+    except G.GhtError as e:
+        return {"scheme": scheme, "n": n, "lf": lf, **cfg, "built": False, "status": e.status}
+    build_ms = _time_ms(lambda: t.build(keys, vals))
+    r = {"scheme": scheme, "n": n, "lf": lf, **cfg, "built": True,
+         "build_gkeys_s": round(n / build_ms / 1e6, 3)}
+    for f in fracs:
+        ms = _time_ms(lambda: t.find(qs[f], out))
+        r[f"find_gkeys_s_f{f}"] = round(n / ms / 1e6, 3)
+    tc = G.HashTable(scheme, n, lf, seed=seed, max_attempts=3, count_probes=1, **cfg)
+    tc.build(keys, vals)
+    r["insert_probes"] = round(tc.stats()["insert_probes"] / n, 4)
+    for f in fracs:
+        tc.reset_counters()
+        tc.find(qs[f], out)
+        r[f"find_probes_f{f}"] = round(tc.stats()["find_probes"] / n, 4)
+    if (scheme, lf) in PAPER_PROBES:
+        r["paper_probes_insert_pos_neg"] = PAPER_PROBES[(scheme, lf)]
+    return r
+
+
 def run_sweep(args, world, rank, local):
     """Config 1 (BCHT, 2^20 keys, LF 0.9, 2^20 queries at 50 % positive: the
     table is L2-resident) and config 2 (2^24 keys; BCHT, P2BHT, IHT, 1CHT with
@@ -697,46 +732,43 @@ def run_sweep(args, world, rank, local):
     B.build()
     rows = []
 
-    def measure(scheme, n, lf, fracs, seed, **cfg):
-        keys, vals = W.make_keys(n, seed, device=dev), W.make_values(n, seed, device=dev)
-        negs = W.make_negatives(n, n, seed, device=dev)
-        qs = {f: W.make_queries(keys, n, f, seed, negs) for f in fracs}
-        out = torch.empty_like(keys)
-        t = G.HashTable(scheme, n, lf, seed=seed, max_attempts=3, **cfg)
-        try:
-            t.build(keys, vals)
-        except G.GhtError as e:
-            return {"scheme": scheme, "n": n, "lf": lf, **cfg, "built": False, "status": e.status}
-        build_ms = _time_ms(lambda: t.build(keys, vals))
-        r = {"scheme": scheme, "n": n, "lf": lf, **cfg, "built": True,
-             "build_gkeys_s": round(n / build_ms / 1e6, 3)}
-        for f in fracs:
-            ms = _time_ms(lambda: t.find(qs[f], out))
-            r[f"find_gkeys_s_f{f}"] = round(n / ms / 1e6, 3)
-        tc = G.HashTable(scheme, n, lf, seed=seed, max_attempts=3, count_probes=1, **cfg)
-        tc.build(keys, vals)
-        r["insert_probes"] = round(tc.stats()["insert_probes"] / n, 4)
-        for f in fracs:
-            tc.reset_counters()
-            tc.find(qs[f], out)
-            r[f"find_probes_f{f}"] = round(tc.stats()["find_probes"] / n, 4)
-        if (scheme, lf) in PAPER_PROBES:
-            r["paper_probes_insert_pos_neg"] = PAPER_PROBES[(scheme, lf)]
-        return r
-
     rows.append({"config": "bcht_n2^20_lf0.9_f0.5 (L2-resident)",
-                 **measure("bcht", 1 << 20, 0.9, (0.5,), SEED + 10)})
+                 **measure_table("bcht", 1 << 20, 0.9, (0.5,), SEED + 10, dev)})
     n = 1 << 24
     for scheme, cfg in (("bcht", {}), ("p2bht", {}), ("iht", {}), ("cuckoo1", {}), ("cuckoo1", {"num_hashes": 4})):
         for lf in (0.6, 0.8, 0.9, 0.95, 0.99):
-            rows.append({"config": "scheme_sweep_n2^24", **measure(scheme, n, lf, (0.0, 0.5, 1.0), SEED + 11, **cfg)})
+            rows.append({"config": "scheme_sweep_n2^24", **measure_table(scheme, n, lf, (0.0, 0.5, 1.0), SEED + 11, dev, **cfg)})
     for scheme, lf in (("p2bht", 0.86), ("iht", 0.86), ("bcht_lb", 0.9), ("bcht_lb", 0.99)):
-        rows.append({"config": "paper_points_n2^24", **measure(scheme, n, lf, (0.0, 1.0), SEED + 12)})
+        rows.append({"config": "paper_points_n2^24", **measure_table(scheme, n, lf, (0.0, 1.0), SEED + 12, dev)})
     for scheme, cfg, lf in (("p2bht", {"bucket_size": 32}, 0.9), ("iht", {"bucket_size": 32}, 0.9)):
-        rows.append({"config": "b32_n2^24", **measure(scheme, n, lf, (0.0, 1.0), SEED + 13, **cfg)})
+        rows.append({"config": "b32_n2^24", **measure_table(scheme, n, lf, (0.0, 1.0), SEED + 13, dev, **cfg)})
     for lf in (0.9, 0.99):
-        rows.append({"config": "keys_only_set_n2^24", **measure("bcht_set", n, lf, (0.0, 0.5, 1.0), SEED + 14)})
+        rows.append({"config": "keys_only_set_n2^24", **measure_table("bcht_set", n, lf, (0.0, 0.5, 1.0), SEED + 14, dev)})
     print(json.dumps({"metric": "scheme sweep: build/find Gkeys/s and probes per key", "workload": "sweep",
+                      "rows": rows}), flush=True)
+
+
+def run_sizes(args, world, rank, local):
+    """Throughput against table size at fixed load factors (the paper's
+    Sec. VII-A size sweeps): BCHT at LF 0.8 and 0.9, P2BHT, IHT and 1CHT at 0.8,
+    P2BHT and IHT with 32-slot buckets at 0.9; 2^16 to 2^26 keys (BCHT to
+    2^28); build, and find at 50 % positive. Small tables are L2-resident."""
+    import torch
+
+    from paper_2108_07232_gb300 import build as B
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+    rows = []
+    cases = [("bcht", 0.8, {}, 28), ("bcht", 0.9, {}, 28), ("p2bht", 0.8, {}, 26), ("iht", 0.8, {}, 26),
+             ("cuckoo1", 0.8, {}, 26), ("p2bht", 0.9, {"bucket_size": 32}, 26), ("iht", 0.9, {"bucket_size": 32}, 26)]
+    for scheme, lf, cfg, top in cases:
+        for lg in range(16, top + 1, 2):
+            r = measure_table(scheme, 1 << lg, lf, (0.5,), SEED + 20 + lg, dev, **cfg)
+            rows.append({"config": f"sizes_{scheme}_lf{lf}", "log2n": lg, **r})
+            torch.cuda.empty_cache()
+    print(json.dumps({"metric": "size sweep: build/find Gkeys/s against keys per table", "workload": "sizes",
                       "rows": rows}), flush=True)
 
 
@@ -802,6 +834,9 @@ def main():
         return
     if args.workload == "success":
         run_success(args, world, rank, local)
+        return
+    if args.workload == "sizes":
+        run_sizes(args, world, rank, local)
         return
     run_ours(args, world, rank, local)
 

@@ -105,7 +105,8 @@ def test_two_phase_from_host_buffers(G):
     assert st["last_build_ranked"] == 1
 
 
-def test_overflow_beyond_the_list_falls_back_to_the_cuckoo_insert(G):
+@pytest.mark.parametrize("group", [-1, 1])
+def test_overflow_beyond_the_list_falls_back_to_the_cuckoo_insert(G, group):
     """6,000 of 20,000 keys share one first-choice bucket under the first
     attempt's constants: far more overflow than the list holds, so that
     attempt inserts every key with the cuckoo insert (or fails and the next
@@ -123,9 +124,10 @@ def test_overflow_beyond_the_list_falls_back_to_the_cuckoo_insert(G):
     assert np.unique(keys_np).size == n
     keys = torch.from_numpy(keys_np.view(np.int32).copy())
     vals = W.make_values(n, 94)
-    t = G.HashTable("bcht", n, lf, seed=seed, count_probes=1, ranked_build=1)
+    t = G.HashTable("bcht", n, lf, seed=seed, count_probes=1, ranked_build=1, group_build=group)
     t.build(keys.cuda(), vals.cuda())
     st = _check(t, O.BCHT, keys, vals, n, lf, 16)
+    assert st["last_build_grouped"] == int(group > 0)
     assert st["attempts"] > 1 or (st["last_build_ranked"] == 0 and st["place_overflow"] > n // 4 + 1024)
 
 
