@@ -716,8 +716,8 @@ def measure_table(scheme, n, lf, fracs, seed, dev, **cfg):
 
 
 def run_sweep(args, world, rank, local):
-    """Config 1 (BCHT, 2^20 keys, LF 0.9, 2^20 queries at 50 % positive: the
-    table is L2-resident) and config 2 (2^24 keys; BCHT, P2BHT, IHT, 1CHT with
+    """The L2-resident case (BCHT, 2^20 keys, LF 0.9, 2^20 queries at 50 %
+    positive) and the scheme sweep at 2^24 keys (BCHT, P2BHT, IHT, 1CHT with
     3 and 4 hash functions; LF 0.6..0.99; positive fraction 0, 0.5, 1): build and
     find throughput per combination, probes per key, and build failures where a
     scheme cannot reach the load factor (expected, Sec. VII-A)."""
