@@ -124,15 +124,15 @@ typedef struct {
   uint64_t table_bytes;        /* device bytes of the table (control block + slots) */
   int32_t built;
   int32_t tile_lanes, keys_per_lane, build_tile_lanes, build_keys_per_lane;
-  /* device time of the last build's fill, grouping and insert kernels and
-   * of the last find kernel, from events on the table's stream (-1 if not
-   * yet complete) */
+  /* device time of the last build's fill, grouping (-1 if not grouped) and
+   * cuckoo insert (in a two-phase build: of the placement's overflow), and of
+   * the last find, from events on the table's stream (-1 if not yet
+   * complete) */
   double last_fill_ms, last_insert_ms, last_find_ms, last_group_ms;
   int32_t last_build_grouped;
   int32_t slot_bytes;          /* 8 for key/value pairs, 4 for GHT_BCHT_SET */
   int32_t last_build_ranked;   /* 1 if the last build was two-phase (ranked placement first) */
-  double last_place_ms;        /* device time of its ranked placement, with the grouping before it
-                                  when grouped (-1 if not two-phase) */
+  double last_place_ms;        /* device time of its ranked placement (-1 if not two-phase) */
   uint64_t place_overflow;     /* keys the ranked placement left to the cuckoo insert */
 } ght_stats_t;
 
@@ -245,7 +245,8 @@ int ght_hash_host(uint32_t a, uint32_t c, uint32_t m, const uint32_t *h_keys, ui
  * are modified in modes 1-3), asynchronously on `cuda_stream` (NULL = legacy
  * default stream). The line of operation i is a mixer of (seed, i) mod
  * num_lines. Modes, after the access patterns of Sec. V:
- *   0  read the whole line (a find's bucket probe, Sec. V-A/V-B);
+ *   0  read the line (one 8-byte word of each 32-byte sector, so DRAM
+ *      delivers all of it: a find's bucket probe, Sec. V-A/V-B);
  *   1  read the line, then one 64-bit CAS into its first slot that depends on
  *      the data read (an insert's probe and CAS, Sec. V-B), results unused;
  *   2  as 1, and each step's CAS results are consumed before the next
