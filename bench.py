@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--build-tile-lanes", type=int, default=0)
     ap.add_argument("--keys-per-lane", type=int, default=0, help="find: query sets in flight per lane")
+    ap.add_argument("--build-keys-per-lane", type=int, default=0, help="insert: keys in flight per lane")
     ap.add_argument("--group-build", type=int, default=0, choices=[-1, 0, 1],
                     help="1: group the pairs by first-choice bucket range before the build")
     ap.add_argument("--ranked-build", type=int, default=0, choices=[-1, 0],
@@ -307,6 +308,8 @@ def run_ours(args, world, rank, local):
         cfg["group_build"] = args.group_build
     if args.keys_per_lane:
         cfg["keys_per_lane"] = args.keys_per_lane
+    if args.build_keys_per_lane:
+        cfg["build_keys_per_lane"] = args.build_keys_per_lane
     tables = {lf: G.HashTable("bcht", n, lf, seed=seed, **cfg) for lf in LFS}
     torch.cuda.synchronize()
 
