@@ -177,7 +177,8 @@ def bytes_per_key(op: str, p: float, lf: float) -> float:
     raise ValueError(op)
 
 
-PROBE_MODES = {0: "random_line_read", 1: "line_read_then_cas", 2: "line_read_then_cas_waited", 3: "atomic_add_only"}
+PROBE_MODES = {0: "random_line_read", 1: "line_read_then_cas", 2: "line_read_then_cas_waited", 3: "atomic_add_only",
+               4: "random_half_line_read", 5: "half_line_then_dependent_sector"}
 
 
 def measure_ceilings(num_lines: int, ops: int, dev, reps: int = 3) -> dict:

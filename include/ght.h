@@ -251,7 +251,9 @@ int ght_hash_host(uint32_t a, uint32_t c, uint32_t m, const uint32_t *h_keys, ui
  *      the data read (an insert's probe and CAS, Sec. V-B), results unused;
  *   2  as 1, and each step's CAS results are consumed before the next
  *      step's reads (one atomic round trip per read);
- *   3  one 64-bit atomic add into a random line, no read.
+ *   3  one 64-bit atomic add into a random line, no read;
+ *   4  read the first half of the line (two 32-byte sectors);
+ *   5  as 4, then one sector of the second half chosen by the data read.
  * Time it with events on the same stream. num_lines must be in [1, 2^32-1]. */
 int ght_probe_lines(int mode, void *d_lines, uint64_t num_lines, uint64_t ops, uint32_t seed, void *cuda_stream);
 

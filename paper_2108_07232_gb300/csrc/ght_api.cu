@@ -912,7 +912,7 @@ int ght_hash_host(uint32_t a, uint32_t c, uint32_t m, const uint32_t *h_keys, ui
 }
 
 int ght_probe_lines(int mode, void *d_lines, uint64_t num_lines, uint64_t ops, uint32_t seed, void *cuda_stream) {
-  if (mode < 0 || mode > 3) return fail(GHT_ERR_INVALID_ARG, "probe mode %d (0..3)", mode);
+  if (mode < 0 || mode > 5) return fail(GHT_ERR_INVALID_ARG, "probe mode %d (0..5)", mode);
   if (!d_lines || (reinterpret_cast<uintptr_t>(d_lines) & 127u))
     return fail(GHT_ERR_INVALID_ARG, "lines must be a 128-byte aligned device pointer");
   if (num_lines == 0 || num_lines > 0xFFFFFFFFull) return fail(GHT_ERR_INVALID_ARG, "num_lines outside [1, 2^32-1]");

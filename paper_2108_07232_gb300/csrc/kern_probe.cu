@@ -24,6 +24,9 @@ __device__ __forceinline__ uint32_t probe_line(uint32_t seed, uint64_t i, const 
 // mode 2: as 1, and the CAS results are consumed before the next reads are
 //         issued (one atomic round trip per read, like an insert that waits).
 // mode 3: one 64-bit atomic add into a random line, no read.
+// mode 4: read the first half of the line (its first two 32-byte sectors).
+// mode 5: read the first half of the line, then one more sector of the
+//         second half chosen by the data (a dependent read).
 // Four lanes cover a line, lane r reading the 8-byte word at byte 32 r (one
 // word of each 32-byte sector, so DRAM delivers the whole line while the
 // registers hold only what is needed to keep many lines in flight); a warp
@@ -49,10 +52,10 @@ line_probe_kernel(unsigned long long *__restrict__ lines, uint32_t num_lines, ui
       ln[u] = i < ops ? probe_line(seed, i, fm) : 0xFFFFFFFFu;
       x[u] = 0;
     }
-    if (mode <= 2) {
+    if (mode <= 2 || mode >= 4) {
 #pragma unroll
       for (int u = 0; u < kProbeUnroll; ++u) {
-        if (ln[u] == 0xFFFFFFFFu) continue;
+        if (ln[u] == 0xFFFFFFFFu || (mode >= 4 && r >= 2)) continue;
         const unsigned long long *p = lines + (uint64_t)ln[u] * 16 + 4 * r;
         if (mode == 0) {
           x[u] = __ldg(p);
@@ -61,7 +64,15 @@ line_probe_kernel(unsigned long long *__restrict__ lines, uint32_t num_lines, ui
         }
       }
     }
-    if (mode >= 1) {
+    if (mode == 5) {
+      // the dependent sector: lane 0 of each line reads a word of sector 2 or 3
+#pragma unroll
+      for (int u = 0; u < kProbeUnroll; ++u) {
+        if (ln[u] == 0xFFFFFFFFu || r != 0) continue;
+        x[u] += __ldg(lines + (uint64_t)ln[u] * 16 + 8 + 4 * (x[u] & 1ull));
+      }
+    }
+    if (mode >= 1 && mode <= 3) {
       unsigned long long s = 0;
 #pragma unroll
       for (int u = 0; u < kProbeUnroll; ++u) {
