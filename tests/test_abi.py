@@ -116,3 +116,17 @@ def test_host_hash_matches_oracle_on_random_and_edge_operands(L):
 def test_host_hash_rejects_zero_buckets(L):
     with pytest.raises(L.GhtError):
         L.ght_hash_host(1, 0, 0, np.zeros(1, np.uint32), np.zeros(1, np.uint32), 1)
+
+
+def test_probe_lines_rejects_bad_arguments_before_any_device_call(L):
+    """The access-pattern probe validates mode, pointer alignment and line
+    count on the host; with ops = 0 a valid call is a no-op. No GPU call."""
+    aligned, misaligned = 1 << 20, (1 << 20) + 8  # never dereferenced: rejected or no-op
+    for mode, ptr, lines in [(-1, aligned, 16), (6, aligned, 16), (0, 0, 16), (0, misaligned, 16),
+                             (0, aligned, 0), (0, aligned, 2**32)]:
+        with pytest.raises(L.GhtError) as e:
+            L.ght_probe_lines(mode, ptr, lines, 1, 1, 0)
+        assert e.value.status == "GHT_ERR_INVALID_ARG", (mode, ptr, lines)
+    for mode in range(6):
+        L.ght_probe_lines(mode, aligned, 16, 0, 1, 0)  # ops = 0: nothing to do
+
