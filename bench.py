@@ -152,7 +152,7 @@ class ClockSampler:
 # from one ncu capture (profiles/bcht_find_n2e28_traffic.md). It describes the
 # kernel source it was captured from, identified by a hash of the find
 # kernel's headers; after any change to them the traffic is reported as null.
-FIND_TRAFFIC = {"bytes_per_launch": 60382687808, "source_sha256_16": "c5a43adc96f0a9f3",
+FIND_TRAFFIC = {"bytes_per_launch": 60378924544, "source_sha256_16": "bebc2909649eb562",
                "kernel": "bucketed_find_kernel"}
 
 
