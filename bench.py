@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--build-tile-lanes", type=int, default=0)
     ap.add_argument("--keys-per-lane", type=int, default=0, help="find: query sets in flight per lane")
     ap.add_argument("--build-keys-per-lane", type=int, default=0, help="insert: keys in flight per lane")
+    ap.add_argument("--find-async", type=int, default=0, choices=[-1, 0, 1])
     ap.add_argument("--group-build", type=int, default=0, choices=[-1, 0, 1],
                     help="1: group the pairs by first-choice bucket range before the build")
     ap.add_argument("--ranked-build", type=int, default=0, choices=[-1, 0],
@@ -152,14 +153,14 @@ class ClockSampler:
 # from one ncu capture (profiles/bcht_find_n2e28_traffic.md). It describes the
 # kernel source it was captured from, identified by a hash of the find
 # kernel's headers; after any change to them the traffic is reported as null.
-FIND_TRAFFIC = {"bytes_per_launch": 60378924544, "source_sha256_16": "bebc2909649eb562",
-               "kernel": "bucketed_find_kernel"}
+FIND_TRAFFIC = {"bytes_per_launch": 60387026112, "source_sha256_16": "4e3475097d517c6d",
+               "kernel": "bcht_find_async_kernel"}
 
 
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("ght_find.cuh", "ght_device.cuh"):
+    for f in ("ght_find.cuh", "ght_find_async.cuh", "ght_device.cuh"):
         with open(os.path.join(ROOT, "paper_2108_07232_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -311,6 +312,8 @@ def run_ours(args, world, rank, local):
         cfg["keys_per_lane"] = args.keys_per_lane
     if args.build_keys_per_lane:
         cfg["build_keys_per_lane"] = args.build_keys_per_lane
+    if args.find_async:
+        cfg["find_async"] = args.find_async
     tables = {lf: G.HashTable("bcht", n, lf, seed=seed, **cfg) for lf in LFS}
     torch.cuda.synchronize()
 
@@ -393,6 +396,7 @@ def run_ours(args, world, rank, local):
     kernels = {}
     st0 = tables[LFS[0]].stats()
     ranked, grouped = bool(st0["last_build_ranked"]), bool(st0["last_build_grouped"])
+    find_name = "bcht_find_async_kernel" if st0["find_staged"] else "bucketed_find_kernel"
     for lf in LFS:
         # a build's work after the fill: the grouping and the ranked placement
         # (when the build does them) and the cuckoo insert, timed together
@@ -410,7 +414,7 @@ def run_ours(args, world, rank, local):
     # dominant kernel = the kernel function with the most device time per step
     build_name = "+".join((["group_count_kernel", "group_scatter_kernel"] if grouped else [])
                           + (["rank_place_kernel"] if ranked else []) + ["bucketed_insert_kernel"])
-    funcs = {"bucketed_find_kernel": [k for k in kernels if k.startswith("find")],
+    funcs = {find_name: [k for k in kernels if k.startswith("find")],
              build_name: [k for k in kernels if k.startswith("build")],
              "fill_kernel": [k for k in kernels if k.startswith("fill")]}
     per_func = {}

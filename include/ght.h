@@ -105,7 +105,13 @@ typedef struct {
    * (ght_build_scratch_bytes), else the build runs the cuckoo insert for
    * every key. */
   int32_t ranked_build;
-  int32_t reserved[2];
+  /* BCHT finds with 16-pair buckets and 4-lane tiles: 1 = stage the bucket
+   * parts in shared memory with asynchronous copies, keys_per_lane (2..8,
+   * default 6) query sets in flight per lane; -1 = off (bucket parts in
+   * registers, keys_per_lane 1..2); 0 = default: on where it applies. Other
+   * shapes reject 1. */
+  int32_t find_async;
+  int32_t reserved[1];
 } ght_config;
 
 typedef struct {
@@ -134,6 +140,8 @@ typedef struct {
   int32_t last_build_ranked;   /* 1 if the last build was two-phase (ranked placement first) */
   double last_place_ms;        /* device time of its ranked placement (-1 if not two-phase) */
   uint64_t place_overflow;     /* keys the ranked placement left to the cuckoo insert */
+  int32_t find_staged;         /* 1 if finds stage bucket parts in shared memory (find_async) */
+  int32_t reserved_stats;
 } ght_stats_t;
 
 /* Library version string; never NULL. */

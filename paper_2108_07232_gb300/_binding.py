@@ -35,7 +35,7 @@ class GhtConfig(C.Structure):
         ("tile_lanes", C.c_int32), ("blocks_per_sm", C.c_int32), ("keys_per_lane", C.c_int32),
         ("build_tile_lanes", C.c_int32), ("build_keys_per_lane", C.c_int32),
         ("build_blocks_per_sm", C.c_int32), ("group_build", C.c_int32), ("ranked_build", C.c_int32),
-        ("reserved", C.c_int32 * 2),
+        ("find_async", C.c_int32), ("reserved", C.c_int32 * 1),
     ]
 
 
@@ -52,6 +52,7 @@ class GhtStats(C.Structure):
         ("last_fill_ms", C.c_double), ("last_insert_ms", C.c_double), ("last_find_ms", C.c_double),
         ("last_group_ms", C.c_double), ("last_build_grouped", C.c_int32), ("slot_bytes", C.c_int32),
         ("last_build_ranked", C.c_int32), ("last_place_ms", C.c_double), ("place_overflow", C.c_uint64),
+        ("find_staged", C.c_int32), ("reserved_stats", C.c_int32),
     ]
 
     def as_dict(self) -> dict:

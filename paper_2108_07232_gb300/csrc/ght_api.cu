@@ -39,6 +39,7 @@ struct Shape {
   int build_tile_lanes, build_blocks_per_sm, build_keys_per_lane;  // build
   int group_build;  // 1: group the input by first-choice bucket range before inserting
   int ranked_build;  // 1: two-phase build (ranked first-choice placement, then cuckoo insert)
+  int find_async;    // 1: BCHT finds stage bucket parts in shared memory
   int slot_bytes;   // 8 (key/value pair) or 4 (keys-only set)
   uint64_t m;
 };
@@ -102,6 +103,7 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
     if (user->build_keys_per_lane) d.build_keys_per_lane = user->build_keys_per_lane;
     d.group_build = user->group_build;
     d.ranked_build = user->ranked_build;
+    d.find_async = user->find_async;
     if (user->threshold) d.threshold = user->threshold;
     else if (scheme == GHT_IHT) d.threshold = (4 * d.bucket_size + 4) / 5;  // ceil(0.8 b)
   }
@@ -126,7 +128,16 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
       if (!ok) return fail(GHT_ERR_INVALID_ARG, "tile of %d lanes unsupported for bucket size %d", g, b);
     }
   }
-  if ((d.keys_per_lane != 1 && d.keys_per_lane != 2) || (d.build_keys_per_lane != 1 && d.build_keys_per_lane != 2))
+  // the staged find: on by default where it applies (BCHT, 16-pair buckets,
+  // 4-lane tiles), with 6 query sets in flight unless keys_per_lane is given
+  const bool staged_shape = scheme == GHT_BCHT && b == 16 && d.tile_lanes == 4;
+  if (d.find_async > 0 && !staged_shape)
+    return fail(GHT_ERR_INVALID_ARG, "the staged find is for BCHT with 16-pair buckets and 4-lane tiles");
+  const bool async_find = d.find_async > 0 || (d.find_async == 0 && staged_shape);
+  if (async_find && !(user && user->keys_per_lane)) d.keys_per_lane = 6;
+  if (async_find ? (d.keys_per_lane < 2 || d.keys_per_lane > 8) : (d.keys_per_lane != 1 && d.keys_per_lane != 2))
+    return fail(GHT_ERR_INVALID_ARG, "keys per lane must be 1 or 2 (2 to 8 for the staged find)");
+  if (d.build_keys_per_lane != 1 && d.build_keys_per_lane != 2)
     return fail(GHT_ERR_INVALID_ARG, "keys per lane must be 1 or 2");
   if (scheme == GHT_IHT && (d.threshold < 1 || d.threshold > b + 1))
     return fail(GHT_ERR_INVALID_ARG, "IHT threshold %d outside [1, b+1]", d.threshold);
@@ -151,6 +162,7 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
   // ranked placement applies to the cuckoo tables with buckets (BCHT and the set)
   s->ranked_build = (scheme == GHT_BCHT || scheme == GHT_BCHT_SET) ? d.ranked_build : -1;
   s->slot_bytes = scheme == GHT_BCHT_SET ? 4 : 8;
+  s->find_async = async_find ? 1 : 0;
   s->m = (uint64_t)want;
   return GHT_OK;
 }
@@ -264,6 +276,7 @@ struct ght_table {
     o.blocks_per_sm = shape.blocks_per_sm;
     o.keys_per_lane = shape.keys_per_lane;
     o.count = shape.count_probes != 0;
+    o.async_find = shape.find_async != 0;
     return o;
   }
 
@@ -359,7 +372,11 @@ cudaError_t launch_place(const ght_table *t, const uint32_t *k, const uint32_t *
 
 cudaError_t launch_find(const ght_table *t, const uint32_t *q, uint32_t *out, uint64_t n) {
   const ght::TableView tv = t->view();
-  if (t->shape.scheme == GHT_BCHT) return ght::launch_find_bcht(t->shape.b, tv, q, out, n, t->find_opts(), t->stream);
+  if (t->shape.scheme == GHT_BCHT) {
+    const ght::LaunchOpts o = t->find_opts();
+    return o.async_find ? ght::launch_find_bcht_async(t->shape.b, tv, q, out, n, o, t->stream)
+                        : ght::launch_find_bcht(t->shape.b, tv, q, out, n, o, t->stream);
+  }
   if (t->shape.scheme == GHT_BCHT_SET) return ght::launch_find_set(tv, q, out, n, t->find_opts(), t->stream);
   return ght::launch_find_other(t->shape.scheme, t->shape.b, tv, q, out, n, t->find_opts(), t->stream);
 }
@@ -848,6 +865,7 @@ int ght_stats(const ght_table *t, ght_stats_t *out) {
   out->last_build_ranked = t->last_ranked ? 1 : 0;
   out->last_place_ms = -1.0;
   out->place_overflow = t->place_overflow;
+  out->find_staged = t->shape.find_async;
   if (t->timed_build && cudaEventQuery(t->tev[3]) == cudaSuccess) {
     if (cudaEventElapsedTime(&ms, t->tev[0], t->tev[1]) == cudaSuccess) out->last_fill_ms = ms;
     // between the fill and the cuckoo insert: the grouping and/or the ranked placement

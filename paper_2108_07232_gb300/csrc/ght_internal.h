@@ -19,6 +19,7 @@ struct LaunchOpts {
   int blocks_per_sm = 0;
   bool count = false;    // probe counters
   bool dynamic = false;  // build: warps claim 32-pair chunks from a global cursor
+  bool async_find = false;  // find: bucket parts staged in shared memory (BCHT, b = 16, 4-lane tiles)
 };
 
 constexpr uint32_t kMaxGroups = 4096;
@@ -79,6 +80,8 @@ cudaError_t launch_insert_bcht(int B, const TableView &tv, const uint32_t *k, co
                                uint64_t n, const LaunchOpts &o, cudaStream_t s);
 cudaError_t launch_find_bcht(int B, const TableView &tv, const uint32_t *q, uint32_t *out,
                              uint64_t n, const LaunchOpts &o, cudaStream_t s);
+cudaError_t launch_find_bcht_async(int B, const TableView &tv, const uint32_t *q, uint32_t *out, uint64_t n,
+                                   const LaunchOpts &o, cudaStream_t s);
 bool bcht_shape_supported(int B, int G);
 
 // kern_set.cu (keys-only BCHT, 32 four-byte keys per bucket)

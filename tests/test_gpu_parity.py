@@ -356,3 +356,56 @@ def test_bcht_build_shapes_at_a_million_keys(G, b, lanes, lf):
     assert S.build(keys, vals) == 1
     gpu, cpu = st["insert_probes"] / n, S.stats.probes / n
     assert abs(gpu - cpu) <= 0.05, (gpu, cpu)
+
+
+@pytest.mark.parametrize("kpl", [2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("lf", [0.9, 0.99])
+def test_staged_find_parity(G, kpl, lf):
+    """The BCHT find that stages bucket parts in shared memory with
+    asynchronous copies, with 2-8 query sets in flight per lane: results
+    bit-exact against the definitional lookup, probe counts equal to the
+    oracle's on the GPU's own table."""
+    t, keys, vals = build_table(G, O.BCHT, N_SMALL, lf, find_async=1, tile_lanes=4, keys_per_lane=kpl)
+    st = t.stats()
+    assert st["keys_per_lane"] == kpl
+    T = oracle_view(st, O.BCHT, N_SMALL, lf)
+    slots = t.export()
+    for f in (0.0, 0.5, 1.0):
+        q = W.make_queries(keys, NQ_SMALL, f, seed=17)
+        t.reset_counters()
+        got = t.find(q.cuda()).cpu()
+        assert (O._u32(got) == O.lookup(keys, vals, q)).all(), f
+        assert t.stats()["find_probes"] == T.find(q, slots=slots)[2]
+    # edge cases: empty input, sentinel queries, a ragged tail
+    empty = torch.empty(0, dtype=torch.int32, device="cuda")
+    assert t.find(empty).numel() == 0
+    q = torch.cat([keys[:5], torch.tensor([-1, -1], dtype=torch.int32), W.make_negatives(N_SMALL, 3, 1)])
+    assert (O._u32(t.find(q.cuda()).cpu()) == O.lookup(keys, vals, q)).all()
+    with pytest.raises(G.GhtError):
+        G.HashTable("bcht", 1000, 0.9, find_async=1, tile_lanes=8)
+    with pytest.raises(G.GhtError):
+        G.HashTable("p2bht", 1000, 0.8, find_async=1)
+    with pytest.raises(G.GhtError):
+        G.HashTable("bcht", 1000, 0.9, find_async=1, keys_per_lane=9)
+
+
+def test_staged_find_is_the_bcht_default(G):
+    """BCHT with 16-pair buckets finds through the staged kernel by default
+    (6 sets per lane); find_async = -1 or another shape selects the register
+    find. Each table's results are bit-exact against the definitional lookup
+    and its probe count equals the oracle's on that table's own slots (the
+    concurrent builds need not lay out the same table)."""
+    keys, vals = W.make_keys(N_SMALL, 23), W.make_values(N_SMALL, 23)
+    q = W.make_queries(keys, NQ_SMALL, 0.5, seed=29)
+    want = O.lookup(keys, vals, q)
+    for cfg, staged, kpl in (({}, 1, 6), ({"find_async": -1}, 0, 2), ({"tile_lanes": 16}, 0, 2)):
+        t = G.HashTable("bcht", N_SMALL, 0.95, seed=5, count_probes=1, **cfg)
+        t.build(keys.cuda(), vals.cuda())
+        st = t.stats()
+        assert (st["find_staged"], st["keys_per_lane"]) == (staged, kpl), cfg
+        T = oracle_view(st, O.BCHT, N_SMALL, 0.95)
+        t.reset_counters()
+        assert (O._u32(t.find(q.cuda()).cpu()) == want).all(), cfg
+        assert t.stats()["find_probes"] == T.find(q, slots=t.export())[2], cfg
+    for s in ("p2bht", "iht", "bcht_lb", "cuckoo1"):
+        assert G.HashTable(s, 1000, 0.8).stats()["find_staged"] == 0
