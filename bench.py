@@ -453,6 +453,7 @@ def run_ours(args, world, rank, local):
         hout = torch.empty_like(hk).pin_memory()
 
         call_ms = {f"{op}@{lf}": [] for lf in LFS for op in ("build", "find_pos", "find_neg")}
+        h2d_gbs = {k: [] for k in call_ms}
 
         def host_step():
             # each call returns once its results are on the host, so the wall
@@ -464,6 +465,9 @@ def run_ours(args, world, rank, local):
                     c0 = time.perf_counter()
                     fn()
                     call_ms[f"{op}@{lf}"].append(1e3 * (time.perf_counter() - c0))
+                    s = t.stats()  # host-to-device copy span of that call (device events)
+                    if s["last_h2d_ms"] > 0:
+                        h2d_gbs[f"{op}@{lf}"].append(s["last_h2d_bytes"] / (s["last_h2d_ms"] / 1e3) / 1e9)
             return int(hout[0])  # the step's result is on the host
 
         host_step()
@@ -479,7 +483,10 @@ def run_ours(args, world, rank, local):
                "h2d_bytes_per_step": len(LFS) * (8 * n + 8 * n),
                "d2h_bytes_per_step": len(LFS) * 8 * n,
                "api": "HashTable.build/find on pinned CPU tensors (ght_build_host / ght_find_host)",
-               "call_ms": {k: round(statistics.median(v), 3) for k, v in call_ms.items()}}
+               "call_ms": {k: round(statistics.median(v), 3) for k, v in call_ms.items()},
+               "call_ms_max": {k: round(max(v), 3) for k, v in call_ms.items()},
+               "h2d_gbs_median_min": {k: [round(statistics.median(v), 1), round(min(v), 1)]
+                                      for k, v in h2d_gbs.items() if v}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

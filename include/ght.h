@@ -108,8 +108,9 @@ typedef struct {
   /* BCHT finds with 16-pair buckets and 4-lane tiles: 1 = stage the bucket
    * parts in shared memory with asynchronous copies, keys_per_lane (2..8,
    * default 6) query sets in flight per lane; -1 = off (bucket parts in
-   * registers, keys_per_lane 1..2); 0 = default: on where it applies. Other
-   * shapes reject 1. */
+   * registers, keys_per_lane 1..2); 0 = default: on where it applies and
+   * the table's slots take at least the device's L2 size. Other shapes
+   * reject 1. */
   int32_t find_async;
   int32_t reserved[1];
 } ght_config;
@@ -142,6 +143,11 @@ typedef struct {
   uint64_t place_overflow;     /* keys the ranked placement left to the cuckoo insert */
   int32_t find_staged;         /* 1 if finds stage bucket parts in shared memory (find_async) */
   int32_t reserved_stats;
+  /* host-to-device copies of the last ght_build_host / ght_find_host call:
+   * device time from its first copy's start to its last copy's end (-1 if
+   * none yet or not complete) and the bytes copied */
+  double last_h2d_ms;
+  uint64_t last_h2d_bytes;
 } ght_stats_t;
 
 /* Library version string; never NULL. */

@@ -83,6 +83,8 @@ int default_config(int scheme, ght_config *c) {
   return GHT_OK;
 }
 
+uint64_t device_l2_bytes();
+
 // Resolve a config against the scheme's defaults and validate the shape.
 int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Shape *s) {
   ght_config d;
@@ -128,15 +130,9 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
       if (!ok) return fail(GHT_ERR_INVALID_ARG, "tile of %d lanes unsupported for bucket size %d", g, b);
     }
   }
-  // the staged find: on by default where it applies (BCHT, 16-pair buckets,
-  // 4-lane tiles), with 6 query sets in flight unless keys_per_lane is given
   const bool staged_shape = scheme == GHT_BCHT && b == 16 && d.tile_lanes == 4;
   if (d.find_async > 0 && !staged_shape)
     return fail(GHT_ERR_INVALID_ARG, "the staged find is for BCHT with 16-pair buckets and 4-lane tiles");
-  const bool async_find = d.find_async > 0 || (d.find_async == 0 && staged_shape);
-  if (async_find && !(user && user->keys_per_lane)) d.keys_per_lane = 6;
-  if (async_find ? (d.keys_per_lane < 2 || d.keys_per_lane > 8) : (d.keys_per_lane != 1 && d.keys_per_lane != 2))
-    return fail(GHT_ERR_INVALID_ARG, "keys per lane must be 1 or 2 (2 to 8 for the staged find)");
   if (d.build_keys_per_lane != 1 && d.build_keys_per_lane != 2)
     return fail(GHT_ERR_INVALID_ARG, "keys per lane must be 1 or 2");
   if (scheme == GHT_IHT && (d.threshold < 1 || d.threshold > b + 1))
@@ -145,6 +141,16 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
   double want = std::ceil((double)capacity / (lf * (double)b));
   if (want < 1.0) want = 1.0;
   if (want > 4294967295.0) return fail(GHT_ERR_INVALID_ARG, "table needs more than 2^32-1 buckets");
+  // the staged find: by default where it applies (BCHT, 16-pair buckets,
+  // 4-lane tiles) and the slots do not fit in the L2 -- there its deeper
+  // pipeline hides DRAM latency; on an L2-resident table the register find's
+  // higher occupancy wins. 6 query sets in flight unless keys_per_lane is given.
+  const uint64_t slot_bytes = scheme == GHT_BCHT_SET ? 4 : 8;
+  const bool async_find =
+      d.find_async > 0 || (d.find_async == 0 && staged_shape && (uint64_t)want * b * slot_bytes >= device_l2_bytes());
+  if (async_find && !(user && user->keys_per_lane)) d.keys_per_lane = 6;
+  if (async_find ? (d.keys_per_lane < 2 || d.keys_per_lane > 8) : (d.keys_per_lane != 1 && d.keys_per_lane != 2))
+    return fail(GHT_ERR_INVALID_ARG, "keys per lane must be 1 or 2 (2 to 8 for the staged find)");
   s->scheme = scheme;
   s->b = b;
   s->h = h;
@@ -161,7 +167,7 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
   s->group_build = d.group_build;
   // ranked placement applies to the cuckoo tables with buckets (BCHT and the set)
   s->ranked_build = (scheme == GHT_BCHT || scheme == GHT_BCHT_SET) ? d.ranked_build : -1;
-  s->slot_bytes = scheme == GHT_BCHT_SET ? 4 : 8;
+  s->slot_bytes = (int)slot_bytes;
   s->find_async = async_find ? 1 : 0;
   s->m = (uint64_t)want;
   return GHT_OK;
@@ -229,8 +235,11 @@ struct ght_table {
   ght::Ctrl *h_ctrl = nullptr;  // pinned mirror of the control block
   cudaEvent_t done = nullptr;
   // timing events: fill start, fill end, pre-insert work end (grouping and/or ranked placement),
-  // insert end, find start, find end, grouping end (when a grouped build also places by rank)
-  cudaEvent_t tev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  // insert end, find start, find end, grouping end (when a grouped build also places by rank),
+  // first and last host-to-device copy of the last host-buffer call
+  cudaEvent_t tev[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  mutable bool timed_h2d = false;
+  mutable uint64_t h2d_bytes = 0;
   bool timed_build = false;
   bool last_grouped = false;
   bool last_ranked = false;
@@ -570,7 +579,7 @@ ght_table *ght_create_ex(int scheme, uint64_t capacity, double load_factor, uint
   t->slots = reinterpret_cast<uint64_t *>(reinterpret_cast<char *>(t->storage) + kCtrlBytes);
   cudaError_t e = cudaMallocHost(reinterpret_cast<void **>(&t->h_ctrl), kCtrlBytes);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->done, cudaEventDisableTiming);
-  for (int i = 0; i < 7 && e == cudaSuccess; ++i) e = cudaEventCreate(&t->tev[i]);
+  for (int i = 0; i < 9 && e == cudaSuccess; ++i) e = cudaEventCreate(&t->tev[i]);
   if (e != cudaSuccess) {
     cuda_fail(e, "creating table resources");
     ght_destroy(t);
@@ -640,9 +649,13 @@ int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_value
   // every pair); so here grouping and ranked placement run only on request.
   const bool ranked_wanted = t->shape.ranked_build > 0 && wants_ranked(t, n);
   if (t->shape.group_build > 0 && wants_grouping(t, n)) {
+    cudaEventRecord(t->tev[7], t->stream);
     if ((e = cudaMemcpyAsync(d_k, h_keys, n * 4, cudaMemcpyHostToDevice, t->stream)) != cudaSuccess ||
         (e = cudaMemcpyAsync(d_v, h_values, n * 4, cudaMemcpyHostToDevice, t->stream)) != cudaSuccess)
       rc = cuda_fail(e, "staging keys");
+    cudaEventRecord(t->tev[8], t->stream);
+    t->timed_h2d = true;
+    t->h2d_bytes = 8 * n;
     if (rc == GHT_OK) rc = build_device(t, d_k, d_v, n, 0);
   } else {
     void *place_pool = nullptr;
@@ -673,6 +686,7 @@ int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_value
         rc = cuda_fail(e, "clearing the arrival counters");
       cudaEventRecord(t->tev[1], t->stream);
       if (!ranked) cudaEventRecord(t->tev[2], t->stream);
+      cudaEventRecord(t->tev[7], copy);
       for (uint64_t off = 0, i = 0; rc == GHT_OK && off < n; off += kChunk, ++i) {
         const uint64_t len = std::min(kChunk, n - off);
         cudaEvent_t ev = landed[i & 1];
@@ -692,6 +706,9 @@ int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_value
           rc = cuda_fail(e, "launching insert");  // each chunk's insert starts its own claims at zero
         }
       }
+      cudaEventRecord(t->tev[8], copy);
+      t->timed_h2d = true;
+      t->h2d_bytes = 8 * n;
       if (rc == GHT_OK && ranked) {
         // phase 2: the cuckoo insert of the keys whose first-choice bucket was full
         cudaEventRecord(t->tev[2], t->stream);
@@ -772,6 +789,7 @@ int ght_find_host(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out
   if (rc == GHT_OK) {
     if ((e = cudaEventRecord(evs[0], t->stream)) != cudaSuccess || (e = cudaStreamWaitEvent(up, evs[0], 0)) != cudaSuccess)
       rc = cuda_fail(e, "ordering the staging copy");
+    cudaEventRecord(t->tev[7], up);
   }
   // events 0..3: "chunk landed" ring; 4..7: "chunk answered" ring. Reusing an
   // event is safe because each stream consumes them in order.
@@ -792,6 +810,11 @@ int ght_find_host(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out
       rc = cuda_fail(e, "returning results");
       break;
     }
+  }
+  if (up) {
+    cudaEventRecord(t->tev[8], up);
+    t->timed_h2d = true;
+    t->h2d_bytes = 4 * n;
   }
   if (rc == GHT_OK) {
     // the table stream frees the buffer after the last read-back
@@ -877,6 +900,12 @@ int ght_stats(const ght_table *t, ght_stats_t *out) {
       else if (t->last_grouped) out->last_group_ms = ms;
     }
     if (cudaEventElapsedTime(&ms, t->tev[2], t->tev[3]) == cudaSuccess) out->last_insert_ms = ms;
+  }
+  out->last_h2d_ms = -1.0;
+  if (t->timed_h2d && cudaEventQuery(t->tev[8]) == cudaSuccess &&
+      cudaEventElapsedTime(&ms, t->tev[7], t->tev[8]) == cudaSuccess) {
+    out->last_h2d_ms = ms;
+    out->last_h2d_bytes = t->h2d_bytes;
   }
   if (t->timed_find && cudaEventQuery(t->tev[5]) == cudaSuccess &&
       cudaEventElapsedTime(&ms, t->tev[4], t->tev[5]) == cudaSuccess)

@@ -58,6 +58,37 @@ inline cudaError_t grid_for(K kernel, uint64_t n, int blocks_per_sm, int *blocks
   return cudaSuccess;
 }
 
+// The same for a kernel with `threads` per block and `smem` bytes of dynamic
+// shared memory; the first call for a kernel also raises its dynamic
+// shared-memory limit to `smem`.
+template <typename K>
+inline cudaError_t grid_for_smem(K kernel, int threads, size_t smem, uint64_t n, int blocks_per_sm, int *blocks_out) {
+  static std::mutex mu;
+  static std::unordered_map<const void *, int> occ_cache;
+  static int sms = 0;
+  std::lock_guard<std::mutex> lock(mu);
+  cudaError_t e;
+  if (sms == 0) {
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  }
+  auto it = occ_cache.find((const void *)kernel);
+  if (it == occ_cache.end()) {
+    if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+      return e;
+    int nb = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem)) != cudaSuccess) return e;
+    it = occ_cache.emplace((const void *)kernel, nb > 0 ? nb : 1).first;
+  }
+  int per_sm = it->second;
+  if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
+  const uint64_t want = (n + threads - 1) / threads;
+  const uint64_t cap = (uint64_t)sms * (uint64_t)per_sm;
+  *blocks_out = (int)(want < cap ? (want > 0 ? want : 1) : cap);
+  return cudaSuccess;
+}
+
 // Warps of a grid share the input in contiguous slices of this many items.
 inline uint64_t per_warp_of(uint64_t n, int blocks) {
   const uint64_t warps = (uint64_t)blocks * (kThreads / 32);

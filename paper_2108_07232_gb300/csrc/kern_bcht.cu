@@ -73,20 +73,11 @@ static cudaError_t find_async_kpl(const TableView &tv, const uint32_t *q, uint32
   auto kern = o.count ? bcht_find_async_kernel<KPL, WARPS, true> : bcht_find_async_kernel<KPL, WARPS, false>;
   constexpr int kBlock = 32 * WARPS;
   const size_t smem = WARPS * find_async_smem_per_warp<KPL>();
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int blocks = 0;
+  cudaError_t e = grid_for_smem(kern, kBlock, smem, n, o.blocks_per_sm, &blocks);
   if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0, per_sm = 0;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
-      (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
-      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, smem)) != cudaSuccess)
-    return e;
-  if (o.blocks_per_sm > 0 && o.blocks_per_sm < per_sm) per_sm = o.blocks_per_sm;
-  if (per_sm < 1) per_sm = 1;
-  const uint64_t want = (n + kBlock - 1) / kBlock;
-  const uint64_t cap = (uint64_t)sms * (uint64_t)per_sm;
-  const uint64_t blocks = want < cap ? (want > 0 ? want : 1) : cap;
-  const uint64_t warps = blocks * WARPS;
-  kern<<<(unsigned)blocks, kBlock, smem, s>>>(tv, q, out, n, (n + warps - 1) / warps);
+  const uint64_t warps = (uint64_t)blocks * WARPS;
+  kern<<<blocks, kBlock, smem, s>>>(tv, q, out, n, (n + warps - 1) / warps);
   return cudaGetLastError();
 }
 

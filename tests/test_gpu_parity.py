@@ -391,14 +391,21 @@ def test_staged_find_parity(G, kpl, lf):
 
 def test_staged_find_is_the_bcht_default(G):
     """BCHT with 16-pair buckets finds through the staged kernel by default
-    (6 sets per lane); find_async = -1 or another shape selects the register
-    find. Each table's results are bit-exact against the definitional lookup
-    and its probe count equals the oracle's on that table's own slots (the
-    concurrent builds need not lay out the same table)."""
+    when its slots do not fit in the L2 (6 sets per lane), through the
+    register find when they do; find_async = 1 / -1 forces either, another
+    tile shape selects the register find. Each table's results are bit-exact
+    against the definitional lookup and its probe count equals the oracle's on
+    that table's own slots (the concurrent builds need not lay out the same
+    table)."""
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    big = G.HashTable("bcht", (l2 // 8) + (1 << 20), 1.0)  # slots beyond the L2
+    assert (big.stats()["find_staged"], big.stats()["keys_per_lane"]) == (1, 6)
+    del big
     keys, vals = W.make_keys(N_SMALL, 23), W.make_values(N_SMALL, 23)
     q = W.make_queries(keys, NQ_SMALL, 0.5, seed=29)
     want = O.lookup(keys, vals, q)
-    for cfg, staged, kpl in (({}, 1, 6), ({"find_async": -1}, 0, 2), ({"tile_lanes": 16}, 0, 2)):
+    for cfg, staged, kpl in (({}, 0, 2), ({"find_async": 1}, 1, 6), ({"find_async": 1, "keys_per_lane": 3}, 1, 3),
+                             ({"find_async": -1}, 0, 2), ({"tile_lanes": 16}, 0, 2)):
         t = G.HashTable("bcht", N_SMALL, 0.95, seed=5, count_probes=1, **cfg)
         t.build(keys.cuda(), vals.cuda())
         st = t.stats()
