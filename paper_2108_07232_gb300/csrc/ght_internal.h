@@ -59,12 +59,13 @@ inline cudaError_t grid_for(K kernel, uint64_t n, int blocks_per_sm, int *blocks
 }
 
 // The same for a kernel with `threads` per block and `smem` bytes of dynamic
-// shared memory; the first call for a kernel also raises its dynamic
-// shared-memory limit to `smem`.
+// shared memory; raises the kernel's dynamic shared-memory limit to `smem`
+// when it is below (occupancy cached per kernel and size).
 template <typename K>
 inline cudaError_t grid_for_smem(K kernel, int threads, size_t smem, uint64_t n, int blocks_per_sm, int *blocks_out) {
   static std::mutex mu;
-  static std::unordered_map<const void *, int> occ_cache;
+  static std::unordered_map<const void *, size_t> limit;                    // per kernel: limit set so far
+  static std::unordered_map<const void *, std::unordered_map<size_t, int>> occ;  // per kernel and size
   static int sms = 0;
   std::lock_guard<std::mutex> lock(mu);
   cudaError_t e;
@@ -73,13 +74,18 @@ inline cudaError_t grid_for_smem(K kernel, int threads, size_t smem, uint64_t n,
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   }
-  auto it = occ_cache.find((const void *)kernel);
-  if (it == occ_cache.end()) {
+  const void *key = (const void *)kernel;
+  if (smem > 48 * 1024 && limit[key] < smem) {
     if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
       return e;
+    limit[key] = smem;
+  }
+  auto &by_size = occ[key];
+  auto it = by_size.find(smem);
+  if (it == by_size.end()) {
     int nb = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem)) != cudaSuccess) return e;
-    it = occ_cache.emplace((const void *)kernel, nb > 0 ? nb : 1).first;
+    it = by_size.emplace(smem, nb > 0 ? nb : 1).first;
   }
   int per_sm = it->second;
   if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
