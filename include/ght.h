@@ -105,12 +105,13 @@ typedef struct {
    * (ght_build_scratch_bytes), else the build runs the cuckoo insert for
    * every key. */
   int32_t ranked_build;
-  /* BCHT finds with 16-pair buckets and 4-lane tiles: 1 = stage the bucket
+  /* Finds of 128-byte buckets (BCHT with 16 pairs and 4-lane tiles; the
+   * keys-only set, whose find tiles then have 4 lanes): 1 = stage the bucket
    * parts in shared memory with asynchronous copies, keys_per_lane (2..8,
    * default 6) query sets in flight per lane; -1 = off (bucket parts in
-   * registers, keys_per_lane 1..2); 0 = default: on where it applies and
-   * the table's slots take at least the device's L2 size. Other shapes
-   * reject 1. */
+   * registers, keys_per_lane 1..2); 0 = default: on where it applies, the
+   * table's slots take at least the device's L2 size and keys_per_lane is
+   * not given as 1. Other shapes reject 1. */
   int32_t find_async;
   int32_t reserved[1];
 } ght_config;

@@ -114,8 +114,11 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
   if (scheme == GHT_BCHT_SET) {
     if (b != 32) return fail(GHT_ERR_INVALID_ARG, "the keys-only set has 32 keys per bucket");
     if (h < 2 || h > 4) return fail(GHT_ERR_INVALID_ARG, "the keys-only set needs 2..4 hash functions");
-    for (int g : {d.tile_lanes, d.build_tile_lanes})
-      if (!ght::set_shape_supported(b, g)) return fail(GHT_ERR_INVALID_ARG, "tile of %d lanes unsupported for the set", g);
+    if (!ght::set_shape_supported(b, d.build_tile_lanes))
+      return fail(GHT_ERR_INVALID_ARG, "tile of %d lanes unsupported for the set", d.build_tile_lanes);
+    // find tiles: 8 lanes, or 4 for the staged find (checked below)
+    if (!ght::set_shape_supported(b, d.tile_lanes) && d.tile_lanes != 4)
+      return fail(GHT_ERR_INVALID_ARG, "tile of %d lanes unsupported for the set", d.tile_lanes);
   } else if (scheme == GHT_CUCKOO1) {
     if (b != 1) return fail(GHT_ERR_INVALID_ARG, "CUCKOO1 has bucket size 1");
     if (h < 2 || h > 4) return fail(GHT_ERR_INVALID_ARG, "CUCKOO1 needs 2..4 hash functions");
@@ -130,9 +133,14 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
       if (!ok) return fail(GHT_ERR_INVALID_ARG, "tile of %d lanes unsupported for bucket size %d", g, b);
     }
   }
-  const bool staged_shape = scheme == GHT_BCHT && b == 16 && d.tile_lanes == 4;
+  // the staged find reads 128-byte buckets (BCHT with 16 pairs, the set with
+  // 32 keys) with 4-lane tiles; the set's default 8-lane find tile gives way
+  // to it unless tile_lanes is given
+  const bool user_tile = user && user->tile_lanes;
+  const bool staged_bucket = (scheme == GHT_BCHT && b == 16) || scheme == GHT_BCHT_SET;
+  const bool staged_shape = staged_bucket && (d.tile_lanes == 4 || (scheme == GHT_BCHT_SET && !user_tile));
   if (d.find_async > 0 && !staged_shape)
-    return fail(GHT_ERR_INVALID_ARG, "the staged find is for BCHT with 16-pair buckets and 4-lane tiles");
+    return fail(GHT_ERR_INVALID_ARG, "the staged find is for 128-byte buckets (BCHT b = 16, the set) and 4-lane tiles");
   if (d.build_keys_per_lane != 1 && d.build_keys_per_lane != 2)
     return fail(GHT_ERR_INVALID_ARG, "keys per lane must be 1 or 2");
   if (scheme == GHT_IHT && (d.threshold < 1 || d.threshold > b + 1))
@@ -141,14 +149,20 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
   double want = std::ceil((double)capacity / (lf * (double)b));
   if (want < 1.0) want = 1.0;
   if (want > 4294967295.0) return fail(GHT_ERR_INVALID_ARG, "table needs more than 2^32-1 buckets");
-  // the staged find: by default where it applies (BCHT, 16-pair buckets,
-  // 4-lane tiles) and the slots do not fit in the L2 -- there its deeper
-  // pipeline hides DRAM latency; on an L2-resident table the register find's
-  // higher occupancy wins. 6 query sets in flight unless keys_per_lane is given.
+  // The staged find by default where it applies and the slots do not fit in
+  // the L2: there its deeper pipeline hides DRAM latency; on an L2-resident
+  // table the register find's higher occupancy wins. A given keys_per_lane of
+  // 1 keeps the register find. 6 query sets in flight unless keys_per_lane is
+  // given.
   const uint64_t slot_bytes = scheme == GHT_BCHT_SET ? 4 : 8;
+  const bool kpl_given = user && user->keys_per_lane;
   const bool async_find =
-      d.find_async > 0 || (d.find_async == 0 && staged_shape && (uint64_t)want * b * slot_bytes >= device_l2_bytes());
-  if (async_find && !(user && user->keys_per_lane)) d.keys_per_lane = 6;
+      d.find_async > 0 || (d.find_async == 0 && staged_shape && !(kpl_given && d.keys_per_lane < 2) &&
+                           (uint64_t)want * b * slot_bytes >= device_l2_bytes());
+  if (async_find && !kpl_given) d.keys_per_lane = 6;
+  if (async_find) d.tile_lanes = 4;
+  if (!async_find && scheme == GHT_BCHT_SET && d.tile_lanes == 4)
+    return fail(GHT_ERR_INVALID_ARG, "4-lane find tiles of the set need the staged find");
   if (async_find ? (d.keys_per_lane < 2 || d.keys_per_lane > 8) : (d.keys_per_lane != 1 && d.keys_per_lane != 2))
     return fail(GHT_ERR_INVALID_ARG, "keys per lane must be 1 or 2 (2 to 8 for the staged find)");
   s->scheme = scheme;
@@ -386,7 +400,11 @@ cudaError_t launch_find(const ght_table *t, const uint32_t *q, uint32_t *out, ui
     return o.async_find ? ght::launch_find_bcht_async(t->shape.b, tv, q, out, n, o, t->stream)
                         : ght::launch_find_bcht(t->shape.b, tv, q, out, n, o, t->stream);
   }
-  if (t->shape.scheme == GHT_BCHT_SET) return ght::launch_find_set(tv, q, out, n, t->find_opts(), t->stream);
+  if (t->shape.scheme == GHT_BCHT_SET) {
+    const ght::LaunchOpts o = t->find_opts();
+    return o.async_find ? ght::launch_find_set_async(tv, q, out, n, o, t->stream)
+                        : ght::launch_find_set(tv, q, out, n, o, t->stream);
+  }
   return ght::launch_find_other(t->shape.scheme, t->shape.b, tv, q, out, n, t->find_opts(), t->stream);
 }
 

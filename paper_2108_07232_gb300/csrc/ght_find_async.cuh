@@ -1,6 +1,6 @@
 // ght_find_async.cuh -- BCHT bulk find with bucket parts staged in shared
-// memory by asynchronous copies (cp.async), for 16-pair buckets read by
-// 4-lane tiles.
+// memory by asynchronous copies (cp.async), for 128-byte buckets (16 pairs,
+// or 32 keys of the keys-only set) read by 4-lane tiles.
 //
 // The probe order, early exit and tile evaluation are those of
 // bucketed_find_kernel (Sec. V-B find). The difference is where a bucket in
@@ -12,6 +12,7 @@
 #pragma once
 
 #include "ght_find.cuh"
+#include "ght_internal.h"
 
 namespace ght {
 
@@ -37,11 +38,12 @@ constexpr size_t find_async_smem_per_warp() {
   return (size_t)KPL * 32 * 8 * 16;
 }
 
-template <int KPL, int WARPS, bool COUNT>
+template <int KPL, int WARPS, bool COUNT, typename S = PairSlot>
 __global__ void __launch_bounds__(32 * WARPS)
 bcht_find_async_kernel(TableView tv, const uint32_t *__restrict__ queries, uint32_t *__restrict__ out, uint64_t n,
                        uint64_t per_warp) {
-  constexpr int B = 16, G = 4;
+  constexpr int G = 4;
+  constexpr bool kPairs = sizeof(typename S::T) == 8;  // else 32-bit keys (a set)
   static_assert(KPL >= 2 && KPL <= 8, "query sets in flight");
   extern __shared__ uint4 fa_smem[];
   const int lane = threadIdx.x & 31;
@@ -84,7 +86,7 @@ bcht_find_async_kernel(TableView tv, const uint32_t *__restrict__ queries, uint3
         if (at < end) {
           if (COUNT) answered++;
           if (k == kEmptyKey) {
-            out[at] = kEmptyKey;  // the sentinel is never a key
+            out[at] = S::missing();  // the sentinel is never a key
           } else {
             active[s] = true;
             key[s] = k;
@@ -102,10 +104,11 @@ bcht_find_async_kernel(TableView tv, const uint32_t *__restrict__ queries, uint3
           const int owner = tbase + j;
           const uint32_t bj = __shfl_sync(kFull, myb, owner);
           if ((act[s] >> owner) & 1u) {
-            const uint64_t *src = tv.slots + (uint64_t)bj * B + 4 * r;  // 32 bytes: slots [4r, 4r + 4)
+            // 32 bytes of the 128-byte bucket: pairs [4r, 4r + 4) or keys [8r, 8r + 8)
+            const uint4 *src = reinterpret_cast<const uint4 *>(tv.slots) + (uint64_t)bj * 8 + 2 * r;
             uint4 *row = sbuf + owner * 8;
             cp_async16(row + ((2u * r) ^ swz), src);
-            cp_async16(row + ((2u * r + 1u) ^ swz), src + 2);
+            cp_async16(row + ((2u * r + 1u) ^ swz), src + 1);
           }
         }
       }
@@ -118,7 +121,7 @@ bcht_find_async_kernel(TableView tv, const uint32_t *__restrict__ queries, uint3
       if (act[e] != 0u) {
         const uint4 *ebuf = wbuf + (size_t)e * 32 * 8;
         bool my_hit = false, my_emp = false;
-        uint32_t my_val = kEmptyKey;
+        uint32_t my_val = S::missing();
 #pragma unroll
         for (int j = 0; j < G; ++j) {
           const int owner = tbase + j;
@@ -129,14 +132,24 @@ bcht_find_async_kernel(TableView tv, const uint32_t *__restrict__ queries, uint3
           if (aj) {
             const uint4 *row = ebuf + owner * 8;
             const uint4 c0 = row[(2u * r) ^ swz], c1 = row[(2u * r + 1u) ^ swz];
-            const uint32_t ks[4] = {c0.x, c0.z, c1.x, c1.z}, vs[4] = {c0.y, c0.w, c1.y, c1.w};
+            if constexpr (kPairs) {
+              const uint32_t ks[4] = {c0.x, c0.z, c1.x, c1.z}, vs[4] = {c0.y, c0.w, c1.y, c1.w};
 #pragma unroll
-            for (int p = 0; p < 4; ++p) {
-              if (ks[p] == kj) {
-                hit = true;
-                hv = vs[p];
+              for (int p = 0; p < 4; ++p) {
+                if (ks[p] == kj) {
+                  hit = true;
+                  hv = vs[p];
+                }
+                emp |= ks[p] == kEmptyKey;
               }
-              emp |= ks[p] == kEmptyKey;
+            } else {
+              const uint32_t ks[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+              for (int p = 0; p < 8; ++p) {
+                hit |= ks[p] == kj;
+                emp |= ks[p] == kEmptyKey;
+              }
+              hv = 1u;
             }
           }
           const unsigned hb = __ballot_sync(kFull, hit) & tmask;
@@ -151,7 +164,7 @@ bcht_find_async_kernel(TableView tv, const uint32_t *__restrict__ queries, uint3
         if ((act[e] >> lane) & 1u) {
           if (COUNT) probes++;
           bool finish = false;
-          uint32_t result = kEmptyKey;
+          uint32_t result = S::missing();
           if (my_hit) {
             result = my_val;
             finish = true;
@@ -185,5 +198,39 @@ bcht_find_async_kernel(TableView tv, const uint32_t *__restrict__ queries, uint3
   }
 }
 
+
+// Launch with KPL sets in flight and WARPS warps per block, as many blocks
+// as are resident at once (shared memory sets the residency, KPL x 4 KB per
+// warp); 2-warp blocks for the deep pipelines keep the resident warps a
+// multiple of the SM's four schedulers (6 sets: 4 blocks, 8 warps per SM).
+template <int KPL, int WARPS, typename S>
+inline cudaError_t launch_staged_find(const TableView &tv, const uint32_t *q, uint32_t *out, uint64_t n, bool count,
+                                      int blocks_per_sm, cudaStream_t s) {
+  auto kern = count ? bcht_find_async_kernel<KPL, WARPS, true, S> : bcht_find_async_kernel<KPL, WARPS, false, S>;
+  constexpr int kBlock = 32 * WARPS;
+  const size_t smem = WARPS * find_async_smem_per_warp<KPL>();
+  int blocks = 0;
+  cudaError_t e = grid_for_smem(kern, kBlock, smem, n, blocks_per_sm, &blocks);
+  if (e != cudaSuccess) return e;
+  const uint64_t warps = (uint64_t)blocks * WARPS;
+  kern<<<blocks, kBlock, smem, s>>>(tv, q, out, n, (n + warps - 1) / warps);
+  return cudaGetLastError();
+}
+
+// keys_per_lane = sets in flight, 2..8
+template <typename S>
+inline cudaError_t launch_staged_find_kpl(const TableView &tv, const uint32_t *q, uint32_t *out, uint64_t n,
+                                          int keys_per_lane, bool count, int blocks_per_sm, cudaStream_t s) {
+  switch (keys_per_lane) {
+    case 2: return launch_staged_find<2, 4, S>(tv, q, out, n, count, blocks_per_sm, s);
+    case 3: return launch_staged_find<3, 4, S>(tv, q, out, n, count, blocks_per_sm, s);
+    case 4: return launch_staged_find<4, 4, S>(tv, q, out, n, count, blocks_per_sm, s);
+    case 5: return launch_staged_find<5, 2, S>(tv, q, out, n, count, blocks_per_sm, s);
+    case 6: return launch_staged_find<6, 2, S>(tv, q, out, n, count, blocks_per_sm, s);
+    case 7: return launch_staged_find<7, 2, S>(tv, q, out, n, count, blocks_per_sm, s);
+    case 8: return launch_staged_find<8, 2, S>(tv, q, out, n, count, blocks_per_sm, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 }  // namespace ght

@@ -119,6 +119,8 @@ cudaError_t launch_find_bcht(int B, const TableView &tv, const uint32_t *q, uint
                              uint64_t n, const LaunchOpts &o, cudaStream_t s);
 cudaError_t launch_find_bcht_async(int B, const TableView &tv, const uint32_t *q, uint32_t *out, uint64_t n,
                                    const LaunchOpts &o, cudaStream_t s);
+cudaError_t launch_find_set_async(const TableView &tv, const uint32_t *q, uint32_t *out, uint64_t n,
+                                  const LaunchOpts &o, cudaStream_t s);
 bool bcht_shape_supported(int B, int G);
 
 // kern_set.cu (keys-only BCHT, 32 four-byte keys per bucket)

@@ -59,41 +59,10 @@ cudaError_t launch_place_bcht(int B, const TableView &tv, const uint32_t *k, con
   return cudaErrorInvalidValue;
 }
 
-// Find with bucket parts staged in shared memory (16-pair buckets, 4-lane
-// tiles, KPL = keys_per_lane sets in flight): blocks of WARPS warps, as many
-// as are resident at once (shared memory sets the count).
-// Find with bucket parts staged in shared memory (16-pair buckets, 4-lane
-// tiles, KPL = keys_per_lane sets in flight): blocks of WARPS warps, as many
-// as are resident at once. Shared memory sets the residency (KPL x 4 KB per
-// warp); 2-warp blocks for the deep pipelines keep the resident warps a
-// multiple of the SM's four schedulers (6 sets: 4 blocks, 8 warps per SM).
-template <int KPL, int WARPS>
-static cudaError_t find_async_kpl(const TableView &tv, const uint32_t *q, uint32_t *out, uint64_t n,
-                                  const LaunchOpts &o, cudaStream_t s) {
-  auto kern = o.count ? bcht_find_async_kernel<KPL, WARPS, true> : bcht_find_async_kernel<KPL, WARPS, false>;
-  constexpr int kBlock = 32 * WARPS;
-  const size_t smem = WARPS * find_async_smem_per_warp<KPL>();
-  int blocks = 0;
-  cudaError_t e = grid_for_smem(kern, kBlock, smem, n, o.blocks_per_sm, &blocks);
-  if (e != cudaSuccess) return e;
-  const uint64_t warps = (uint64_t)blocks * WARPS;
-  kern<<<blocks, kBlock, smem, s>>>(tv, q, out, n, (n + warps - 1) / warps);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_find_bcht_async(int B, const TableView &tv, const uint32_t *q, uint32_t *out, uint64_t n,
                                    const LaunchOpts &o, cudaStream_t s) {
   if (B != 16 || o.tile_lanes != 4) return cudaErrorInvalidValue;
-  switch (o.keys_per_lane) {
-    case 2: return find_async_kpl<2, 4>(tv, q, out, n, o, s);
-    case 3: return find_async_kpl<3, 4>(tv, q, out, n, o, s);
-    case 4: return find_async_kpl<4, 4>(tv, q, out, n, o, s);
-    case 5: return find_async_kpl<5, 2>(tv, q, out, n, o, s);
-    case 6: return find_async_kpl<6, 2>(tv, q, out, n, o, s);
-    case 7: return find_async_kpl<7, 2>(tv, q, out, n, o, s);
-    case 8: return find_async_kpl<8, 2>(tv, q, out, n, o, s);
-    default: return cudaErrorInvalidValue;
-  }
+  return launch_staged_find_kpl<PairSlot>(tv, q, out, n, o.keys_per_lane, o.count, o.blocks_per_sm, s);
 }
 
 bool bcht_shape_supported(int B, int G) {

@@ -4,6 +4,7 @@
 // Sec. I and Sec. III-A).
 #include "ght_internal.h"
 #include "ght_kernels.cuh"
+#include "ght_find_async.cuh"
 
 namespace ght {
 
@@ -55,6 +56,14 @@ cudaError_t launch_find_set(const TableView &tv, const uint32_t *q, uint32_t *ou
                             cudaStream_t s) {
   if (o.tile_lanes != 8) return cudaErrorInvalidValue;
   return o.keys_per_lane == 1 ? set_find<1>(tv, q, out, n, o, s) : set_find<2>(tv, q, out, n, o, s);
+}
+
+// The staged find (bucket parts in shared memory, 4-lane tiles, keys_per_lane
+// sets in flight) on the set's 32-key buckets.
+cudaError_t launch_find_set_async(const TableView &tv, const uint32_t *q, uint32_t *out, uint64_t n,
+                                  const LaunchOpts &o, cudaStream_t s) {
+  if (o.tile_lanes != 4) return cudaErrorInvalidValue;
+  return launch_staged_find_kpl<KeySlot>(tv, q, out, n, o.keys_per_lane, o.count, o.blocks_per_sm, s);
 }
 
 }  // namespace ght

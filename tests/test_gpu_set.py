@@ -66,3 +66,47 @@ def test_keys_only_set_edges(G):
         t.build(torch.tensor([1, -1], dtype=torch.int32).cuda())
     with pytest.raises(G.GhtError):
         G.HashTable("bcht_set", 100, 0.9, bucket_size=16)
+
+
+@pytest.mark.parametrize("lf", [0.9, 0.99])
+@pytest.mark.parametrize("kpl", [4, 6])
+def test_keys_only_set_staged_find(G, lf, kpl):
+    """The staged find (bucket parts in shared memory, 4-lane tiles) on the
+    set's 32-key buckets: membership bit-exact against the definitional
+    lookup, probe counts equal to the oracle's on the exported table, the
+    sentinel answered absent."""
+    n = (1 << 16) + 29
+    keys = W.make_keys(n, 67)
+    zeros = torch.zeros(n, dtype=torch.int32)
+    t = G.HashTable("bcht_set", n, lf, seed=3, count_probes=1, find_async=1, keys_per_lane=kpl)
+    t.build(keys.cuda())
+    st = t.stats()
+    assert (st["find_staged"], st["tile_lanes"], st["keys_per_lane"]) == (1, 4, kpl)
+    T = O.Table(O.BCHT, n, lf, b=32, m=st["num_buckets"])
+    T.set_constants(st["hash_a"], st["hash_c"])
+    pairs = _as_pairs(t.export())
+    for f in (0.0, 0.5, 1.0):
+        q = W.make_queries(keys, n + 7, f, seed=11)
+        t.reset_counters()
+        got = O._u32(t.find(q.cuda()).cpu())
+        want = (O.lookup(keys, zeros, q) != O.EMPTY).astype(np.uint32)
+        assert (got == want).all(), f
+        assert t.stats()["find_probes"] == T.find(q, slots=pairs)[2]
+    q = torch.cat([keys[:3], torch.tensor([-1], dtype=torch.int32), W.make_negatives(n, 2, 3)])
+    assert O._u32(t.find(q.cuda()).cpu()).tolist() == [1, 1, 1, 0, 0, 0]
+
+
+def test_keys_only_set_find_selection(G):
+    """Small sets find through the 8-lane register find, sets whose slots
+    exceed the L2 through the staged one; the forms that cannot run are
+    rejected."""
+    small = G.HashTable("bcht_set", 1 << 16, 0.9).stats()
+    assert (small["find_staged"], small["tile_lanes"]) == (0, 8)
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    big = G.HashTable("bcht_set", (l2 // 4) + (1 << 20), 1.0)
+    assert (big.stats()["find_staged"], big.stats()["tile_lanes"], big.stats()["keys_per_lane"]) == (1, 4, 6)
+    del big
+    with pytest.raises(G.GhtError):
+        G.HashTable("bcht_set", 1000, 0.9, find_async=1, tile_lanes=8)
+    with pytest.raises(G.GhtError):
+        G.HashTable("bcht_set", 1000, 0.9, find_async=-1, tile_lanes=4)
