@@ -77,6 +77,30 @@ def test_table_bytes_rejects_bad_shapes(L):
     assert L.ght_table_bytes(2, 100, 0.9, {"bucket_size": 32}) > 0  # IHT b = 32, t = 26
 
 
+def test_staged_find_shapes(L):
+    """The staged find applies to 128-byte buckets read by 4-lane tiles with
+    2..8 query sets per lane; every other combination is refused before any
+    device call (the sizing itself is unchanged by it)."""
+    ok = L.ght_table_bytes(0, 1000, 0.9)
+    for kpl in range(2, 9):
+        assert L.ght_table_bytes(0, 1000, 0.9, {"find_async": 1, "keys_per_lane": kpl}) == ok
+    assert L.ght_table_bytes(0, 1000, 0.9, {"find_async": 1, "keys_per_lane": 1}) == 0
+    assert L.ght_table_bytes(0, 1000, 0.9, {"find_async": 1, "keys_per_lane": 9}) == 0
+    assert L.ght_table_bytes(0, 1000, 0.9, {"find_async": 1, "tile_lanes": 16}) == 0
+    assert L.ght_table_bytes(0, 1000, 0.9, {"find_async": 1, "bucket_size": 32, "tile_lanes": 8}) == 0
+    for scheme in (1, 2, 3, 4):  # P2BHT, IHT, 1CHT, load-balanced BCHT
+        assert L.ght_table_bytes(scheme, 1000, 0.8, {"find_async": 1}) == 0
+    # the register find keeps 1..2 sets per lane
+    assert L.ght_table_bytes(0, 1000, 0.9, {"find_async": -1, "keys_per_lane": 3}) == 0
+    # the keys-only set: 4-lane find tiles only with the staged find
+    set_ok = L.ght_table_bytes(5, 1000, 0.9)
+    assert L.ght_table_bytes(5, 1000, 0.9, {"find_async": 1}) == set_ok
+    assert L.ght_table_bytes(5, 1000, 0.9, {"find_async": 1, "tile_lanes": 4, "keys_per_lane": 8}) == set_ok
+    assert L.ght_table_bytes(5, 1000, 0.9, {"find_async": 1, "tile_lanes": 8}) == 0
+    assert L.ght_table_bytes(5, 1000, 0.9, {"find_async": -1, "tile_lanes": 4}) == 0
+    assert L.ght_table_bytes(5, 1000, 0.9, {"tile_lanes": 4}) == 0  # small: no staged find by default
+
+
 def _host_hash(L, a, c, m, keys):
     keys = np.ascontiguousarray(keys, dtype=np.uint32)
     out = np.empty_like(keys)
