@@ -21,7 +21,8 @@
  *     misses, or that queries GHT_EMPTY, returns GHT_EMPTY. A stored value equal
  *     to GHT_EMPTY cannot be told apart from a miss.
  *   - Keys passed to one build must be unique (the paper's inputs are unique,
- *     Sec. VII); duplicates are a precondition violation, not detected.
+ *     Sec. VII); duplicates are a precondition violation, detected only when
+ *     the config's check_duplicates is set.
  *   - Pointers named d_* are device memory owned by the caller (for example
  *     torch tensors, int32 reinterpreted as uint32); the library never frees
  *     them. Pointers named h_* are host memory owned by the caller.
@@ -67,7 +68,8 @@ typedef enum {
   GHT_ERR_NOT_BUILT = 5,       /* find on a table without a successful build */
   GHT_ERR_CUDA = 6,            /* a CUDA runtime call failed */
   GHT_ERR_DEVICE_TIMEOUT = 7,  /* a bounded device or host wait ran out */
-  GHT_ERR_CAPACITY = 8         /* n larger than the table's capacity */
+  GHT_ERR_CAPACITY = 8,        /* n larger than the table's capacity */
+  GHT_ERR_DUPLICATE_KEY = 9    /* check_duplicates found a key stored more than once */
 } ght_status;
 
 typedef struct ght_table ght_table; /* opaque, library-owned */
@@ -83,7 +85,8 @@ typedef struct {
   int32_t count_probes;  /* 1: kernels accumulate probe counters (slower; off for timing) */
   /* Launch shapes (0 = tuned default). Find: lanes that read one bucket
    * together (4, 8 or 16; 8 or 16 for 32-pair buckets; 8 for schemes other
-   * than BCHT), queries each lane keeps in flight (1 or 2), blocks per SM.
+   * than BCHT; 4 for the staged find, see find_async), queries each lane
+   * keeps in flight (1 or 2; 2..8 for the staged find), blocks per SM.
    * Build: the same three for the insert kernel. */
   int32_t tile_lanes;
   int32_t blocks_per_sm;
@@ -113,7 +116,11 @@ typedef struct {
    * table's slots take at least the device's L2 size and keys_per_lane is
    * not given as 1. Other shapes reject 1. */
   int32_t find_async;
-  int32_t reserved[1];
+  /* 1: after a successful ght_build / ght_build_host, check that no input key
+   * is stored more than once (every candidate bucket of every input key is
+   * read: a debug aid, off by default). A duplicate fails the call with
+   * GHT_ERR_DUPLICATE_KEY and leaves the table unbuilt. */
+  int32_t check_duplicates;
 } ght_config;
 
 typedef struct {

@@ -17,7 +17,7 @@ SCHEMES = {"bcht": BCHT, "p2bht": P2BHT, "iht": IHT, "cuckoo1": CUCKOO1, "bcht_l
 STATUS = {
     0: "GHT_OK", 1: "GHT_ERR_INVALID_ARG", 2: "GHT_ERR_OOM", 3: "GHT_ERR_BUILD_FAILED",
     4: "GHT_ERR_SENTINEL_KEY", 5: "GHT_ERR_NOT_BUILT", 6: "GHT_ERR_CUDA",
-    7: "GHT_ERR_DEVICE_TIMEOUT", 8: "GHT_ERR_CAPACITY",
+    7: "GHT_ERR_DEVICE_TIMEOUT", 8: "GHT_ERR_CAPACITY", 9: "GHT_ERR_DUPLICATE_KEY",
 }
 
 
@@ -35,7 +35,7 @@ class GhtConfig(C.Structure):
         ("tile_lanes", C.c_int32), ("blocks_per_sm", C.c_int32), ("keys_per_lane", C.c_int32),
         ("build_tile_lanes", C.c_int32), ("build_keys_per_lane", C.c_int32),
         ("build_blocks_per_sm", C.c_int32), ("group_build", C.c_int32), ("ranked_build", C.c_int32),
-        ("find_async", C.c_int32), ("reserved", C.c_int32 * 1),
+        ("find_async", C.c_int32), ("check_duplicates", C.c_int32),
     ]
 
 
@@ -196,7 +196,10 @@ def _config(cfg) -> GhtConfig | None:
     if cfg is None or isinstance(cfg, GhtConfig):
         return cfg
     c = GhtConfig()
+    names = {f for f, _ in GhtConfig._fields_}
     for k, v in dict(cfg).items():
+        if k not in names:
+            raise TypeError(f"unknown table option {k!r}")
         if v is not None:
             setattr(c, k, int(v))
     return c

@@ -40,6 +40,7 @@ struct Shape {
   int group_build;  // 1: group the input by first-choice bucket range before inserting
   int ranked_build;  // 1: two-phase build (ranked first-choice placement, then cuckoo insert)
   int find_async;    // 1: BCHT finds stage bucket parts in shared memory
+  int check_dups;    // 1: a successful build checks that no key is stored twice
   int slot_bytes;   // 8 (key/value pair) or 4 (keys-only set)
   uint64_t m;
 };
@@ -106,6 +107,7 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
     d.group_build = user->group_build;
     d.ranked_build = user->ranked_build;
     d.find_async = user->find_async;
+    d.check_duplicates = user->check_duplicates;
     if (user->threshold) d.threshold = user->threshold;
     else if (scheme == GHT_IHT) d.threshold = (4 * d.bucket_size + 4) / 5;  // ceil(0.8 b)
   }
@@ -183,6 +185,7 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
   s->ranked_build = (scheme == GHT_BCHT || scheme == GHT_BCHT_SET) ? d.ranked_build : -1;
   s->slot_bytes = (int)slot_bytes;
   s->find_async = async_find ? 1 : 0;
+  s->check_dups = d.check_duplicates > 0 ? 1 : 0;
   s->m = (uint64_t)want;
   return GHT_OK;
 }
@@ -523,6 +526,23 @@ int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n,
 
 constexpr uint64_t kChunk = 1ull << 23;  // keys per host<->device pipeline chunk
 
+// check_duplicates: after a successful build from device keys, no key may be
+// stored twice; a duplicate leaves the table unbuilt.
+int check_duplicates(ght_table *t, const uint32_t *d_keys, uint64_t n) {
+  if (!t->shape.check_dups || !t->built || n == 0) return GHT_OK;
+  const cudaError_t e = ght::launch_dup_check(t->view(), t->shape.b, t->shape.scheme == GHT_BCHT_SET, d_keys, n,
+                                              t->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the duplicate check");
+  const int rc = read_ctrl(t);
+  if (rc) return rc;
+  if (t->h_ctrl->status & ght::kStatusDuplicate) {
+    t->built = false;
+    t->n_stored = 0;
+    return fail(GHT_ERR_DUPLICATE_KEY, "an input key is stored more than once (duplicate keys)");
+  }
+  return GHT_OK;
+}
+
 }  // namespace
 
 bool ght::table_descriptor(const ght_table *t, ght::BatchTable *out) {
@@ -624,7 +644,8 @@ int ght_build(ght_table *t, const uint32_t *d_keys, const uint32_t *d_values, ui
                                    (unsigned long long)t->capacity);
   if (n > 0 && (!d_keys || (!d_values && t->shape.scheme != GHT_BCHT_SET)))
     return fail(GHT_ERR_INVALID_ARG, "keys or values is NULL");
-  return build_device(t, d_keys, d_values, n, 0);
+  const int rc = build_device(t, d_keys, d_values, n, 0);
+  return rc == GHT_OK ? check_duplicates(t, d_keys, n) : rc;
 }
 
 int ght_find(const ght_table *t, const uint32_t *d_queries, uint32_t *d_out, uint64_t n) {
@@ -773,6 +794,7 @@ int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_value
     // the staged copy is complete: the table stream waited on every chunk
     if (rc == GHT_OK && (retry_staged || retry_next)) rc = build_device(t, d_k, d_v, n, retry_next ? 1 : 0);
   }
+  if (rc == GHT_OK) rc = check_duplicates(t, d_k, n);  // on the staged copy, before it is freed
   cudaFreeAsync(buf, t->stream);
   if (rc == GHT_OK) {
     e = cudaEventRecord(t->done, t->stream);

@@ -19,7 +19,8 @@ enum : uint32_t {
   kStatusBuildFailed = 1u,  // chain bound hit or all candidate buckets full
   kStatusTimeout = 2u,      // a per-key step bound ran out
   kStatusSentinel = 4u,     // an input key was the sentinel
-  kStatusCorrupt = 8u       // an evicted key did not hash to its bucket
+  kStatusCorrupt = 8u,      // an evicted key did not hash to its bucket
+  kStatusDuplicate = 16u    // the duplicate check found a key stored twice
 };
 
 // Device control block, at the start of a table's storage (256 bytes).

@@ -139,6 +139,8 @@ cudaError_t launch_find_other(int scheme, int B, const TableView &tv, const uint
                               uint32_t *out, uint64_t n, const LaunchOpts &o, cudaStream_t s);
 bool other_shape_supported(int scheme, int B, int G);
 cudaError_t launch_fill(const TableView &tv, uint64_t num_slots, cudaStream_t s);
+cudaError_t launch_dup_check(const TableView &tv, int B, bool key_slots, const uint32_t *keys, uint64_t n,
+                             cudaStream_t s);
 cudaError_t launch_hash(const TableView &tv, const uint32_t *k, uint32_t *out, uint64_t n,
                         cudaStream_t s);
 

@@ -106,6 +106,45 @@ cudaError_t launch_find_other(int scheme, int B, const TableView &tv, const uint
   GHT_DISPATCH_BUCKETED(find_shape, tv, q, out, n, o, s)
 }
 
+// Debug check after a successful build (keys must be unique, Sec. VII): every
+// scheme stores a key only in its candidate buckets H_0 .. H_{h-1}, so an
+// input key with more than one copy across its distinct candidate buckets was
+// passed more than once. Thread per key, every slot of every candidate read.
+template <typename S>
+__global__ void __launch_bounds__(256)
+dup_check_kernel(TableView tv, int B, const uint32_t *__restrict__ keys, uint64_t n) {
+  using T = typename S::T;
+  const T *slots = reinterpret_cast<const T *>(tv.slots);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint32_t k = __ldg(keys + i);
+    if (k == kEmptyKey) continue;  // rejected by the build already
+    uint32_t seen[4];
+    int copies = 0;
+    for (int f = 0; f < tv.h && f < 4; ++f) {
+      const uint32_t b = bucket_of(tv.hf, f, k);
+      bool again = false;
+      for (int g = 0; g < f; ++g) again |= seen[g] == b;
+      seen[f] = b;
+      if (again) continue;
+      for (int j = 0; j < B; ++j) copies += S::key(slots[(uint64_t)b * B + j]) == k;
+    }
+    if (copies > 1) atomicOr(&tv.ctrl->status, (uint32_t)kStatusDuplicate);
+  }
+}
+
+cudaError_t launch_dup_check(const TableView &tv, int B, bool key_slots, const uint32_t *keys, uint64_t n,
+                             cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  if (B < 1 || B > 32) return cudaErrorInvalidValue;
+  int blocks = 0;
+  auto kern = key_slots ? dup_check_kernel<KeySlot> : dup_check_kernel<PairSlot>;
+  cudaError_t e = grid_for(kern, n, 0, &blocks);
+  if (e != cudaSuccess) return e;
+  kern<<<blocks, kThreads, 0, s>>>(tv, B, keys, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fill(const TableView &tv, uint64_t num_slots, cudaStream_t s) {
   const uint64_t n16 = num_slots / 2;  // slots start 256-byte aligned
   uint64_t *tail = (num_slots & 1) ? tv.slots + (num_slots - 1) : nullptr;

@@ -416,3 +416,40 @@ def test_staged_find_is_the_bcht_default(G):
         assert t.stats()["find_probes"] == T.find(q, slots=t.export())[2], cfg
     for s in ("p2bht", "iht", "bcht_lb", "cuckoo1"):
         assert G.HashTable(s, 1000, 0.8).stats()["find_staged"] == 0
+
+
+@pytest.mark.parametrize("scheme,lf", [("bcht", 0.9), ("p2bht", 0.8), ("iht", 0.8), ("cuckoo1", 0.5),
+                                       ("bcht_lb", 0.9), ("bcht_set", 0.9)])
+def test_duplicate_key_check(G, scheme, lf):
+    """Keys must be unique (Sec. VII). With check_duplicates a build whose
+    input holds a key twice fails with GHT_ERR_DUPLICATE_KEY and leaves the
+    table unbuilt; unique input passes the check and finds as usual; without
+    the check the same input builds (the precondition is not tested)."""
+    n = 20000
+    keys = W.make_keys(n, 71)
+    vals = W.make_values(n, 71)
+    dup_k = keys.clone()
+    dup_k[n - 1] = dup_k[17]  # one key twice
+    sets = scheme == "bcht_set"
+    t = G.HashTable(scheme, n, lf, seed=5, check_duplicates=1)
+    t.build(keys.cuda(), None if sets else vals.cuda())
+    assert t.stats()["built"] == 1
+    q = W.make_queries(keys, 4096, 0.5, seed=3)
+    got = O._u32(t.find(q.cuda()).cpu())
+    want = O.lookup(keys, vals, q)
+    if sets:
+        want = (want != O.EMPTY).astype(np.uint32)
+    assert (got == want).all()
+    for src in ("device", "host"):
+        kk = dup_k.cuda() if src == "device" else dup_k.pin_memory()
+        vv = None if sets else (vals.cuda() if src == "device" else vals.pin_memory())
+        with pytest.raises(G.GhtError) as err:
+            t.build(kk, vv)
+        assert err.value.status == "GHT_ERR_DUPLICATE_KEY", src
+        assert t.stats()["built"] == 0
+        with pytest.raises(G.GhtError):
+            t.find(q.cuda())
+    if scheme != "cuckoo1":  # a repeated key can lengthen a 1CHT chain past its bound
+        u = G.HashTable(scheme, n, lf, seed=5)
+        u.build(dup_k.cuda(), None if sets else vals.cuda())
+        assert u.stats()["built"] == 1
