@@ -153,7 +153,7 @@ class ClockSampler:
 # from one ncu capture (profiles/bcht_find_n2e28_traffic.md). It describes the
 # kernel source it was captured from, identified by a hash of the find
 # kernel's headers; after any change to them the traffic is reported as null.
-FIND_TRAFFIC = {"bytes_per_launch": 60386853120, "source_sha256_16": "43927b4d826733dd",
+FIND_TRAFFIC = {"bytes_per_launch": 60386213504, "source_sha256_16": "a0ac993b7e41992f",
                "kernel": "bcht_find_async_kernel"}
 
 
