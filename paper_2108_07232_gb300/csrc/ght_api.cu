@@ -815,6 +815,7 @@ int ght_find_host(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out
   const uint64_t nchunks = (n + kChunk - 1) / kChunk;
   cudaEvent_t evs[8] = {};
   int rc = GHT_OK;
+  bool h2d_started = false;  // the copy-span start event was recorded in this call
   cudaError_t e = pool_alloc(reinterpret_cast<void **>(&d_buf), 2 * n * sizeof(uint32_t), t->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -829,7 +830,7 @@ int ght_find_host(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out
   if (rc == GHT_OK) {
     if ((e = cudaEventRecord(evs[0], t->stream)) != cudaSuccess || (e = cudaStreamWaitEvent(up, evs[0], 0)) != cudaSuccess)
       rc = cuda_fail(e, "ordering the staging copy");
-    cudaEventRecord(t->tev[7], up);
+    h2d_started = rc == GHT_OK && cudaEventRecord(t->tev[7], up) == cudaSuccess;
   }
   // events 0..3: "chunk landed" ring; 4..7: "chunk answered" ring. Reusing an
   // event is safe because each stream consumes them in order.
@@ -851,7 +852,7 @@ int ght_find_host(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out
       break;
     }
   }
-  if (up) {
+  if (h2d_started) {
     cudaEventRecord(t->tev[8], up);
     t->timed_h2d = true;
     t->h2d_bytes = 4 * n;

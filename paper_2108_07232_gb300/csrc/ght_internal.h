@@ -59,34 +59,38 @@ inline cudaError_t grid_for(K kernel, uint64_t n, int blocks_per_sm, int *blocks
 }
 
 // The same for a kernel with `threads` per block and `smem` bytes of dynamic
-// shared memory; raises the kernel's dynamic shared-memory limit to `smem`
-// when it is below (occupancy cached per kernel and size).
+// shared memory; raises the kernel's dynamic shared-memory limit on the
+// current device to `smem` when it is below. Attribute, SM count and
+// occupancy are cached per device (the attribute is a per-device setting).
 template <typename K>
 inline cudaError_t grid_for_smem(K kernel, int threads, size_t smem, uint64_t n, int blocks_per_sm, int *blocks_out) {
+  struct PerDevice {
+    int sms = 0;
+    std::unordered_map<const void *, size_t> limit;                          // per kernel: limit set so far
+    std::unordered_map<const void *, std::unordered_map<size_t, int>> occ;  // per kernel and size
+  };
   static std::mutex mu;
-  static std::unordered_map<const void *, size_t> limit;                    // per kernel: limit set so far
-  static std::unordered_map<const void *, std::unordered_map<size_t, int>> occ;  // per kernel and size
-  static int sms = 0;
+  static std::unordered_map<int, PerDevice> devices;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(mu);
-  cudaError_t e;
-  if (sms == 0) {
-    int dev = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  }
+  PerDevice &d = devices[dev];
+  if (d.sms == 0 && (e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   const void *key = (const void *)kernel;
-  if (smem > 48 * 1024 && limit[key] < smem) {
+  if (smem > 48 * 1024 && d.limit[key] < smem) {
     if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
       return e;
-    limit[key] = smem;
+    d.limit[key] = smem;
   }
-  auto &by_size = occ[key];
+  auto &by_size = d.occ[key];
   auto it = by_size.find(smem);
   if (it == by_size.end()) {
     int nb = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem)) != cudaSuccess) return e;
     it = by_size.emplace(smem, nb > 0 ? nb : 1).first;
   }
+  const int sms = d.sms;
   int per_sm = it->second;
   if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
   const uint64_t want = (n + threads - 1) / threads;
