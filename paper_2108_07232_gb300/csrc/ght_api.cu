@@ -39,7 +39,7 @@ struct Shape {
   int build_tile_lanes, build_blocks_per_sm, build_keys_per_lane;  // build
   int group_build;  // 1: group the input by first-choice bucket range before inserting
   int ranked_build;  // 1: two-phase build (ranked first-choice placement, then cuckoo insert)
-  int find_async;    // 1: BCHT finds stage bucket parts in shared memory
+  int find_async;    // 1: finds stage bucket parts in shared memory (BCHT b = 16, the set)
   int check_dups;    // 1: a successful build checks that no key is stored twice
   int slot_bytes;   // 8 (key/value pair) or 4 (keys-only set)
   uint64_t m;
