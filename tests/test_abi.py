@@ -154,3 +154,13 @@ def test_probe_lines_rejects_bad_arguments_before_any_device_call(L):
     for mode in range(6):
         L.ght_probe_lines(mode, aligned, 16, 0, 1, 0)  # ops = 0: nothing to do
 
+
+
+def test_unknown_table_options_are_rejected(L):
+    """A misspelt option must not be dropped silently: the binding refuses
+    names that are not fields of ght_config (before any device call)."""
+    with pytest.raises(TypeError):
+        L.ght_table_bytes(0, 1000, 0.9, {"find_asynk": 1})
+    with pytest.raises(TypeError):
+        L.ght_table_bytes(0, 1000, 0.9, {"reserved": 0})
+    assert L.ght_table_bytes(0, 1000, 0.9, {"check_duplicates": 1}) == L.ght_table_bytes(0, 1000, 0.9)
