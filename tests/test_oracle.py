@@ -114,6 +114,56 @@ def test_xorshift32_is_a_permutation_of_nonzero_states():
     assert len(set(xs)) == len(xs)
 
 
+def test_xorshift32_hand_derived_vector(golden_dir):
+    rows = _read_rows(os.path.join(golden_dir, "xorshift32_seed1.txt"))
+    assert O.xorshift32_stream(1, len(rows)) == [int(r[0]) for r in rows]
+
+
+def test_xorshift32_has_full_period():
+    """Marsaglia (2003) lists (13, 17, 5) among the shift triples whose 32-bit
+    xorshift generator has period 2^32 - 1. The step is linear over GF(2):
+    its matrix T (column j = the step applied to bit j) must satisfy
+    T^(2^32-1) = I and T^((2^32-1)/q) != I for every prime q dividing
+    2^32 - 1 = 3 * 5 * 17 * 257 * 65537. A wrong shift amount or direction
+    breaks this."""
+    def step(x):
+        return O.xorshift32_stream(x, 1)[0]
+
+    rng = random.Random(5)
+    for _ in range(100):
+        x, y = rng.randrange(1, 2**32), rng.randrange(1, 2**32)
+        if x != y:
+            assert step(x ^ y) == step(x) ^ step(y)
+    cols = [step(1 << j) for j in range(32)]
+
+    def apply(m, v):
+        r, j = 0, 0
+        while v:
+            if v & 1:
+                r ^= m[j]
+            v >>= 1
+            j += 1
+        return r
+
+    def mul(a, b):  # a after b
+        return [apply(a, bc) for bc in b]
+
+    def power(m, e):
+        r = [1 << j for j in range(32)]
+        while e:
+            if e & 1:
+                r = mul(m, r)
+            m = mul(m, m)
+            e >>= 1
+        return r
+
+    ident = [1 << j for j in range(32)]
+    order = 2**32 - 1
+    assert power(cols, order) == ident
+    for q in (3, 5, 17, 257, 65537):
+        assert power(cols, order // q) != ident, q
+
+
 def test_sizing(golden_dir):
     for n, lf, b, m in _read_rows(os.path.join(golden_dir, "sizing.txt")):
         assert O.num_buckets(int(n), float(lf), int(b)) == int(m), (n, lf, b)
@@ -144,7 +194,7 @@ def test_lookup_rejects_sentinel_key():
 
 # ------------------------------------------------------------ worked example ---
 
-_SCHEMES = {"bcht": O.BCHT, "p2bht": O.P2BHT, "iht": O.IHT, "cuckoo1": O.CUCKOO1}
+_SCHEMES = {"bcht": O.BCHT, "p2bht": O.P2BHT, "iht": O.IHT, "cuckoo1": O.CUCKOO1, "bcht_lb": O.BCHT_LB}
 
 
 def _fixture_table(case):
@@ -154,7 +204,7 @@ def _fixture_table(case):
     for k, hs in case["hashes"].items():
         eb[int(k)] = hs
     T = O.Table(_SCHEMES[case["scheme"]], 16, 1.0, b=b, h=h, m=m, t=case.get("t"),
-                explicit_buckets=eb, max_chain=8)
+                explicit_buckets=eb, max_chain=case.get("max_chain", 8))
     T.slots[:] = O.EMPTY_PAIR
     for bi, ks in enumerate(case["initial"]):
         for s, k in enumerate(ks):
@@ -187,6 +237,9 @@ def test_fig1_worked_examples(golden_dir):
             moved = [k for k, bkt in before.items() if _bucket_of(T, k) != bkt]
             assert len(moved) == 1 and before[moved[0]] == e["moved_from"]
             assert _bucket_of(T, moved[0]) == e["moved_to"]
+        if "moves" in e:  # (from, to) of every key that changed bucket
+            moves = sorted([before[k], _bucket_of(T, k)] for k in before if _bucket_of(T, k) != before[k])
+            assert moves == sorted(e["moves"]), case["name"]
         # values travel with their keys
         for pair in T.slots:
             if int(pair) != O.EMPTY_PAIR:
@@ -227,10 +280,12 @@ def test_probe_counts_match_the_paper(golden_dir, probe_inputs):
 
 
 def test_find_closed_forms(probe_inputs):
-    """Negative finds: exactly 2 probes for P2BHT and 3 for IHT (no early
-    exit), at most h for BCHT; 50 % positive = mean of 0 % and 100 %."""
+    """Negative finds: exactly 2 probes for P2BHT and 3 for IHT and the
+    load-balanced BCHT (no early exit, Sec. III-A last paragraph), at most h
+    for BCHT; 50 % positive = mean of 0 % and 100 %."""
     n, keys, vals, qpos, qneg = probe_inputs
-    for scheme, lf, neg_exact in ((O.P2BHT, 0.8, 2), (O.IHT, 0.86, 3), (O.BCHT, 0.95, None)):
+    for scheme, lf, neg_exact in ((O.P2BHT, 0.8, 2), (O.IHT, 0.86, 3), (O.BCHT, 0.95, None),
+                                  (O.BCHT_LB, 0.95, 3)):
         T = O.Table(scheme, n, lf, seed=9)
         assert T.build(keys, vals) == 1
         vpos, pp, tp = T.find(qpos)
@@ -343,6 +398,32 @@ def test_validator_catches_broken_early_exit_invariant():
             break
     ok, msg = T.validate(keys, vals)
     assert not ok and "not full" in msg
+
+
+def test_validator_catches_broken_iht_threshold_invariant():
+    """Sec. III-C: a key goes to a secondary bucket only when its primary
+    would reach t keys. A key moved from its primary (holding fewer than
+    t - 1 keys) to a secondary with room breaks this, and the validator says
+    so."""
+    n = 3000
+    keys, vals = W.make_keys(n, 6), W.make_values(n, 6)
+    T = O.Table(O.IHT, n, 0.6, seed=1)
+    assert T.build(keys, vals) == 1 and T.params.t == 13
+    assert T.validate(keys, vals)[0]
+    s = T.slots
+    for i, pair in enumerate(s):
+        if int(pair) == O.EMPTY_PAIR:
+            continue
+        k = int(pair) & 0xFFFFFFFF
+        bp, bs = T.bucket(0, k), T.bucket(1, k)
+        if i // T.b == bp and bs != bp and T.load(bp) <= T.params.t - 1 and T.load(bs) < T.b:
+            dest = bs * T.b + next(j for j in range(T.b) if int(s[bs * T.b + j]) == O.EMPTY_PAIR)
+            s[dest], s[i] = pair, np.uint64(O.EMPTY_PAIR)
+            break
+    else:
+        pytest.fail("no key to move")
+    ok, msg = T.validate(keys, vals)
+    assert not ok and "primary" in msg
 
 
 # -------------------------------------------------------------- brute force ---
