@@ -31,6 +31,9 @@
  *     stream once per attempt to read the build status.
  *   - Functions return a ght_status; on error ght_last_error() gives a
  *     thread-local message. No C++ exception crosses this ABI.
+ *   - Every host wait for the device polls an event with a deadline: the
+ *     environment variable GHT_WAIT_TIMEOUT_S in seconds (default 300); when
+ *     it runs out the call returns GHT_ERR_DEVICE_TIMEOUT.
  *   - The hash family is h_i(k) = ((a_i k + c_i) mod p) mod m, p = 4294967291
  *     (Sec. VII setup; the paper writes b for c_i). a_i, c_i come from SplitMix64
  *     seeded with seed XOR (attempt * 0x9E3779B97F4A7C15), drawn a_0, c_0, a_1, ...
@@ -121,6 +124,15 @@ typedef struct {
    * read: a debug aid, off by default). A duplicate fails the call with
    * GHT_ERR_DUPLICATE_KEY and leaves the table unbuilt. */
   int32_t check_duplicates;
+  /* Per-key step bound of the bucketed insert kernels: a key that has made
+   * this many bucket visits (reads, CAS retries and exchanges together) stops,
+   * sets the table's timeout status and the build returns
+   * GHT_ERR_DEVICE_TIMEOUT with the table unbuilt (no retry with new
+   * constants). 0 = derived: (max_chain + 2) * h * (b + 2) + 64, which a
+   * correct insert never reaches (every visit stores the key, exchanges, or
+   * loses a CAS to a slot that stays filled). A smaller value only serves to
+   * test that the device loop ends and the error reaches the caller. */
+  uint32_t max_steps;
 } ght_config;
 
 typedef struct {
@@ -203,7 +215,10 @@ int ght_find(const ght_table *t, const uint32_t *d_queries, uint32_t *d_out, uin
 /* As ght_build / ght_find with HOST arrays: the library stages them in
  * device memory from its own stream-ordered pool (find pipelines chunked
  * host<->device copies with the kernel) and returns when the table is built
- * or the results are in h_out. Pinned host memory copies fastest. */
+ * or the results are in h_out. Pinned host memory copies fastest. If the
+ * bounded wait for the device runs out (GHT_ERR_DEVICE_TIMEOUT, see
+ * GHT_WAIT_TIMEOUT_S), copies already queued may still read h_keys/h_values
+ * or write h_out afterwards. */
 int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_values, uint64_t n);
 int ght_find_host(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out, uint64_t n);
 
@@ -215,19 +230,24 @@ int ght_find_host(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out
  * staging buffers are allocated per call.
  *
  * The queries are copied into a staging array that is part of the library
- * image (a static device array of 2 x GHT_NOALLOC_MAX_QUERIES uint32, 32 MiB,
- * held on every GPU that loads the library until the process exits), found
- * there by the ordinary find kernel, and the results are copied back into
- * h_out before the call returns. n must not exceed GHT_NOALLOC_MAX_QUERIES
- * (else GHT_ERR_CAPACITY, nothing is done); n = 0 is a no-op. The table must
- * have been built and its device must be current.
+ * image (a static device array of 2 x GHT_NOALLOC_MAX_QUERIES uint32, 32 MiB),
+ * found there by the ordinary find kernel, and the results are copied back
+ * into h_out before the call returns. n must not exceed
+ * GHT_NOALLOC_MAX_QUERIES (else GHT_ERR_CAPACITY, nothing is done); n = 0 is
+ * a no-op. The table must have been built, and the device current at its
+ * creation must be current (else GHT_ERR_INVALID_ARG, nothing is done).
  *
- * The first call on a device looks up the staging array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * Every call on a device shares the one staging array, whose contents are
- * whatever the last call left there: calls that overlap on the GPU (from
- * several host threads or streams at once) race on it and must be
- * serialised by the caller. */
+ * The array is reserved on a device when the first table is created there:
+ * ght_create / ght_create_ex look up its device address once per device
+ * (cudaGetSymbolAddress, which has the driver load it), so this call itself
+ * neither allocates nor loads anything. The array then stays reserved on that
+ * device until the process exits. Every call on a device shares it, and its
+ * contents are whatever the last call left there: calls that overlap on the
+ * GPU (from several host threads or streams at once) race on it and must be
+ * serialised by the caller. If the wait for the device runs out
+ * (GHT_ERR_DEVICE_TIMEOUT), the copies may still be running and may still
+ * write h_out; later calls on that device return GHT_ERR_DEVICE_TIMEOUT until
+ * they have finished. */
 #define GHT_NOALLOC_MAX_QUERIES (1u << 22)
 int ght_find_host_noalloc(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out, uint64_t n);
 

@@ -35,7 +35,7 @@ class GhtConfig(C.Structure):
         ("tile_lanes", C.c_int32), ("blocks_per_sm", C.c_int32), ("keys_per_lane", C.c_int32),
         ("build_tile_lanes", C.c_int32), ("build_keys_per_lane", C.c_int32),
         ("build_blocks_per_sm", C.c_int32), ("group_build", C.c_int32), ("ranked_build", C.c_int32),
-        ("find_async", C.c_int32), ("check_duplicates", C.c_int32),
+        ("find_async", C.c_int32), ("check_duplicates", C.c_int32), ("max_steps", C.c_uint32),
     ]
 
 

@@ -42,6 +42,7 @@ struct Shape {
   int find_async;    // 1: finds stage bucket parts in shared memory (BCHT b = 16, the set)
   int check_dups;    // 1: a successful build checks that no key is stored twice
   int slot_bytes;   // 8 (key/value pair) or 4 (keys-only set)
+  uint32_t max_steps;  // per-key step bound of the insert kernels (0: derived)
   uint64_t m;
 };
 
@@ -108,6 +109,7 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
     d.ranked_build = user->ranked_build;
     d.find_async = user->find_async;
     d.check_duplicates = user->check_duplicates;
+    d.max_steps = user->max_steps;
     if (user->threshold) d.threshold = user->threshold;
     else if (scheme == GHT_IHT) d.threshold = (4 * d.bucket_size + 4) / 5;  // ceil(0.8 b)
   }
@@ -186,6 +188,7 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
   s->slot_bytes = (int)slot_bytes;
   s->find_async = async_find ? 1 : 0;
   s->check_dups = d.check_duplicates > 0 ? 1 : 0;
+  s->max_steps = d.max_steps;
   s->m = (uint64_t)want;
   return GHT_OK;
 }
@@ -233,8 +236,53 @@ ght::PlaceBuffers place_buffers(char *scr, uint64_t m, uint64_t n) {
 
 }  // namespace
 
+// Static staging array of the allocation-free host find
+// (ght_find_host_noalloc). It is a file-scope device variable, so no
+// allocator is involved once it exists; but with lazy module loading the
+// driver creates it (32 MiB) only when the host first asks for its address.
+// That first lookup therefore happens when a table is created on a device --
+// a call that allocates anyway -- never inside the allocation-free call.
+// In host code the name g_noalloc_staging is only a host-side stand-in: the
+// device address is looked up once per device, with that device current,
+// and passed to the copies and the kernel.
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) uint32_t g_noalloc_staging[2ull * GHT_NOALLOC_MAX_QUERIES];
+
+struct NoAllocDevice {
+  uint32_t *base = nullptr;     // device address of g_noalloc_staging on this device
+  cudaEvent_t pending = nullptr;  // completion of a call that timed out
+  bool busy = false;            // a timed-out call may still use the array
+  bool failed = false;          // set-up failed on this device
+};
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc[kNoAllocMaxDevices];
+
+// Once per device, with that device current: resolve the staging array's
+// device address and create the event that tracks a timed-out call.
+void noalloc_setup(int dev) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  NoAllocDevice &d = g_noalloc[dev];
+  if (d.base || d.failed) return;
+  void *p = nullptr;
+  cudaEvent_t ev = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_staging) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    d.failed = true;
+    return;
+  }
+  d.base = static_cast<uint32_t *>(p);
+  d.pending = ev;
+}
+
+}  // namespace
+
 struct ght_table {
   Shape shape;
+  int device = 0;  // the device current at creation, where the storage lives
   uint64_t capacity = 0;
   double lf = 0;
   uint64_t seed = 0;
@@ -290,9 +338,10 @@ struct ght_table {
     v.rng_seed = rng_seed;
     // Every bucket visit ends in a stored key, an exchange, or a failed CAS
     // that fills one more slot for good, so a key needs at most
-    // (max_chain + 1) visits of at most h * (b + 1) reads each.
+    // (max_chain + 1) visits of at most h * (b + 1) reads each. A configured
+    // bound replaces the derived one.
     const uint64_t steps = ((uint64_t)shape.max_chain + 2ull) * (uint64_t)shape.h * ((uint64_t)shape.b + 2ull) + 64ull;
-    v.max_steps = (uint32_t)std::min<uint64_t>(steps, 0xFFFFFFF0ull);
+    v.max_steps = shape.max_steps ? shape.max_steps : (uint32_t)std::min<uint64_t>(steps, 0xFFFFFFF0ull);
     return v;
   }
 
@@ -591,12 +640,18 @@ ght_table *ght_create_ex(int scheme, uint64_t capacity, double load_factor, uint
       return nullptr;
     }
   }
+  int dev = 0;
+  if (const cudaError_t e = cudaGetDevice(&dev); e != cudaSuccess) {
+    cuda_fail(e, "querying the current device");
+    return nullptr;
+  }
   ght_table *t = new (std::nothrow) ght_table();
   if (!t) {
     fail(GHT_ERR_OOM, "host allocation failed");
     return nullptr;
   }
   t->shape = s;
+  t->device = dev;
   t->capacity = capacity;
   t->lf = load_factor;
   t->seed = seed;
@@ -625,6 +680,7 @@ ght_table *ght_create_ex(int scheme, uint64_t capacity, double load_factor, uint
   }
   memset(t->h_ctrl, 0, kCtrlBytes);
   t->derive(0);
+  noalloc_setup(dev);  // reserves the allocation-free find's staging array on this device
   return t;
 }
 
@@ -1026,20 +1082,8 @@ void ght_destroy(ght_table *t) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// Host-buffer find without allocation (declared in ght.h). The staging array
-// is a file-scope device variable, so it exists as soon as the library's
-// device code is loaded on a GPU and no allocator is involved. In host code
-// the name g_noalloc_staging is only a host-side stand-in, so the device
-// address is looked up once per device and passed to the copies and kernel.
-namespace {
-
-constexpr int kNoAllocMaxDevices = 64;
-static __device__ __align__(256) uint32_t g_noalloc_staging[2ull * GHT_NOALLOC_MAX_QUERIES];
-std::mutex g_noalloc_mu;
-uint32_t *g_noalloc_ptr[kNoAllocMaxDevices] = {};
-
-}  // namespace
-
+// Host-buffer find without allocation (declared in ght.h), on the static
+// staging array set up when the table was created.
 extern "C" int ght_find_host_noalloc(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out,
                                      uint64_t n) {
   if (!t) return fail(GHT_ERR_INVALID_ARG, "table is NULL");
@@ -1052,18 +1096,24 @@ extern "C" int ght_find_host_noalloc(const ght_table *t, const uint32_t *h_queri
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "querying the current device");
+  if (dev != t->device)
+    return fail(GHT_ERR_INVALID_ARG, "device %d is current but the table lives on device %d", dev, t->device);
   if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(GHT_ERR_INVALID_ARG, "device %d out of range", dev);
   uint32_t *base = nullptr;
+  cudaEvent_t pending = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-      // set-up, once per device, with that device current
-      void *p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_noalloc_staging);
-      if (e != cudaSuccess) return cuda_fail(e, "looking up the static staging array");
-      g_noalloc_ptr[dev] = static_cast<uint32_t *>(p);
+    NoAllocDevice &d = g_noalloc[dev];
+    if (!d.base) return fail(GHT_ERR_CUDA, "the static staging array could not be set up on device %d", dev);
+    if (d.busy) {
+      const cudaError_t q = cudaEventQuery(d.pending);
+      if (q == cudaErrorNotReady)
+        return fail(GHT_ERR_DEVICE_TIMEOUT, "an earlier call that timed out still uses the staging array");
+      if (q != cudaSuccess) return cuda_fail(q, "querying the earlier call");
+      d.busy = false;
     }
-    base = g_noalloc_ptr[dev];
+    base = d.base;
+    pending = d.pending;
   }
   uint32_t *d_q = base, *d_o = base + GHT_NOALLOC_MAX_QUERIES;
   e = cudaMemcpyAsync(d_q, h_queries, n * sizeof(uint32_t), cudaMemcpyHostToDevice, t->stream);
@@ -1074,5 +1124,13 @@ extern "C" int ght_find_host_noalloc(const ght_table *t, const uint32_t *h_queri
   if (e != cudaSuccess) return cuda_fail(e, "copying results back");
   e = cudaEventRecord(t->done, t->stream);
   if (e != cudaSuccess) return cuda_fail(e, "recording an event");
-  return wait_event(t->done);
+  const int rc = wait_event(t->done);
+  if (rc == GHT_ERR_DEVICE_TIMEOUT) {
+    // the copies may still run: later calls on this device wait for them
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (cudaEventRecord(pending, t->stream) == cudaSuccess) g_noalloc[dev].busy = true;
+    cudaGetLastError();
+    return fail(GHT_ERR_DEVICE_TIMEOUT, "the find did not finish in time; h_out may still be written");
+  }
+  return rc;
 }

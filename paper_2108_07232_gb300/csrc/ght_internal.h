@@ -27,33 +27,35 @@ constexpr uint32_t kMaxGroups = 4096;
 constexpr int kThreads = 256;
 
 // Grid for a persistent-style launch: at most as many blocks as are resident
-// at once (SMs x blocks per SM), never more than the work needs.
+// at once (SMs x blocks per SM), never more than the work needs. SM count and
+// occupancy are cached per device.
 template <typename K>
 inline cudaError_t grid_for(K kernel, uint64_t n, int blocks_per_sm, int *blocks_out) {
+  struct PerDevice {
+    int sms = 0;
+    std::unordered_map<const void *, int> occ;  // per kernel: resident blocks per SM
+  };
   static std::mutex mu;
-  static std::unordered_map<const void *, int> occ_cache;
-  static int sms = 0;
+  static std::unordered_map<int, PerDevice> devices;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(mu);
-  if (sms == 0) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-  }
+  PerDevice &d = devices[dev];
+  if (d.sms == 0 && (e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   int per_sm = blocks_per_sm;
   if (per_sm <= 0) {
-    auto it = occ_cache.find((const void *)kernel);
-    if (it == occ_cache.end()) {
+    auto it = d.occ.find((const void *)kernel);
+    if (it == d.occ.end()) {
       int nb = 0;
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kThreads, 0);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kThreads, 0);
       if (e != cudaSuccess) return e;
-      it = occ_cache.emplace((const void *)kernel, nb > 0 ? nb : 1).first;
+      it = d.occ.emplace((const void *)kernel, nb > 0 ? nb : 1).first;
     }
     per_sm = it->second;
   }
   const uint64_t want = (n + kThreads - 1) / kThreads;
-  const uint64_t cap = (uint64_t)sms * (uint64_t)per_sm;
+  const uint64_t cap = (uint64_t)d.sms * (uint64_t)per_sm;
   *blocks_out = (int)(want < cap ? (want > 0 ? want : 1) : cap);
   return cudaSuccess;
 }

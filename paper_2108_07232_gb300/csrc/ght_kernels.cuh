@@ -512,7 +512,11 @@ rank_place_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint32_
 // ----------------------------------------------------------------------------
 // Bucket size one cuckoo ("1CHT", Sec. VII; CUDPP style): one thread per
 // key, each step a single 64-bit exchange into H_i(k); a displaced pair moves
-// on to H_{(i+1) mod h}. Fails once more than max_chain pairs were displaced.
+// on to H_{(i+1) mod h}. With b = 1 the exchange is also the bucket read.
+// Sec. III-A fails an insert once the maximum number of exchanges has been
+// made and the next bucket is full: so after max_chain displacements the
+// next step is a CAS into an empty slot, and a full slot there fails the
+// build without displacing another pair.
 template <bool COUNT>
 __global__ void __launch_bounds__(256)
 cuckoo1_insert_kernel(TableView tv, const uint32_t *__restrict__ keys,
@@ -532,16 +536,18 @@ cuckoo1_insert_kernel(TableView tv, const uint32_t *__restrict__ keys,
     uint32_t cur = bucket_of(tv.hf, 0, k0);
     uint32_t displaced = 0;
     for (;;) {
-      const uint64_t old = exch_pair(tv.slots + cur, pair);
+      const bool at_bound = displaced >= tv.max_chain;
+      const uint64_t old = at_bound ? cas_pair(tv.slots + cur, kEmptyPair, pair) : exch_pair(tv.slots + cur, pair);
       if (COUNT) probes++;
       if (pair_key(old) == kEmptyKey) break;
-      if (COUNT) {
-        evictions++;
-        if (displaced + 1 > longest) longest = displaced + 1;
-      }
-      if (++displaced > tv.max_chain) {
+      if (at_bound) {
         atomicOr(&tv.ctrl->status, kStatusBuildFailed);
         break;
+      }
+      ++displaced;
+      if (COUNT) {
+        evictions++;
+        if (displaced > longest) longest = displaced;
       }
       pair = old;
       const uint32_t k = pair_key(old);

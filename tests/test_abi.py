@@ -164,3 +164,52 @@ def test_unknown_table_options_are_rejected(L):
     with pytest.raises(TypeError):
         L.ght_table_bytes(0, 1000, 0.9, {"reserved": 0})
     assert L.ght_table_bytes(0, 1000, 0.9, {"check_duplicates": 1}) == L.ght_table_bytes(0, 1000, 0.9)
+
+
+def _header():
+    return open(os.path.join(ROOT, "include", "ght.h")).read()
+
+
+def test_noalloc_capacity_matches_the_header(L):
+    """The binding's copy of GHT_NOALLOC_MAX_QUERIES is the header's value."""
+    m = re.search(r"#define\s+GHT_NOALLOC_MAX_QUERIES\s+\((\d+)u\s*<<\s*(\d+)\)", _header())
+    assert m, "GHT_NOALLOC_MAX_QUERIES not found in ght.h"
+    assert L.NOALLOC_MAX_QUERIES == int(m.group(1)) << int(m.group(2))
+
+
+def _struct_fields(src, name):
+    end = re.search(r"\}\s*" + name + ";", src).start()
+    body = src[src.rindex("typedef struct {", 0, end) + len("typedef struct {"):end]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        typ, ptr, names = re.match(r"(?:const\s+)?(\w+)\s*(\*?)\s*(.*)", decl, re.S).groups()
+        for nm in names.split(","):
+            nm = nm.strip()
+            arr = re.match(r"(\w+)\[(\d+)\]", nm)
+            t = "pointer" if ptr else typ
+            fields.append((arr.group(1), t, int(arr.group(2))) if arr else (nm, t, 1))
+    return fields
+
+
+@pytest.mark.parametrize("cname,pyname", [("ght_config", "GhtConfig"), ("ght_stats_t", "GhtStats"),
+                                          ("ght_batch_stats_t", "GhtBatchStats"),
+                                          ("ght_pool_result_t", "GhtPoolResult"),
+                                          ("ght_pool_stats_t", "GhtPoolStats"),
+                                          ("ght_pool_request_t", "GhtPoolRequest")])
+def test_binding_structs_follow_the_header(L, cname, pyname):
+    """Each ctypes structure of the binding lists the header's fields in the
+    header's order with the same sizes, so no field is read from the wrong
+    offset."""
+    import ctypes as C
+
+    from paper_2108_07232_gb300 import _binding
+    sizes = {"int32_t": 4, "uint32_t": 4, "uint64_t": 8, "double": 8, "pointer": C.sizeof(C.c_void_p)}
+    want = _struct_fields(_header(), cname)
+    got = getattr(_binding, pyname)._fields_
+    assert [f[0] for f in want] == [g[0] for g in got]
+    for (name, typ, count), (_, ctype) in zip(want, got):
+        assert C.sizeof(ctype) == sizes[typ] * count, name

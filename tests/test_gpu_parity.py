@@ -85,12 +85,15 @@ def test_build_and_find_parity(G, scheme, lf):
 
 @pytest.mark.parametrize("scheme,lf,tol", [(O.BCHT, 0.9, 0.03), (O.BCHT, 0.99, 0.05),
                                            (O.P2BHT, 0.8, 0.0), (O.IHT, 0.86, 0.05),
-                                           (O.CUCKOO1, 0.85, 0.1)])
+                                           (O.CUCKOO1, 0.85, 0.1),
+                                           (O.BCHT_LB, 0.9, 0.02), (O.BCHT_LB, 0.99, 0.05)])
 def test_insert_probes_match_sequential_oracle(G, scheme, lf, tol):
     """Cuckoo and two-choice inserts read, on average, as many buckets as the
-    sequential oracle. IHT decides from the primary's load at read time; with
-    many keys in flight those loads lag, fewer keys spill to the secondaries,
-    and the GPU reads fewer buckets than the oracle (never more)."""
+    sequential oracle; the load-balanced BCHT reads all h candidates per step
+    (3 per key until evictions start). IHT decides from the primary's load at
+    read time; with many keys in flight those loads lag, fewer keys spill to
+    the secondaries, and the GPU reads fewer buckets than the oracle (never
+    more)."""
     n = 1 << 22
     t, keys, vals = build_table(G, scheme, n, lf, seed=3)
     st = t.stats()
@@ -453,3 +456,109 @@ def test_duplicate_key_check(G, scheme, lf):
         u = G.HashTable(scheme, n, lf, seed=5)
         u.build(dup_k.cuda(), None if sets else vals.cuda())
         assert u.stats()["built"] == 1
+
+
+@pytest.mark.parametrize("b,t,lf", [(16, 4, 0.86), (16, 7, 0.86), (16, 10, 0.86), (16, 13, 0.86),
+                                    (32, 7, 0.9), (32, 13, 0.9), (32, 20, 0.9), (32, 26, 0.9)])
+def test_iht_threshold_sweep_parity(G, b, t, lf):
+    """Sec. VII-A3 sweeps the IHT threshold over 20/40/60/80 % of the bucket
+    size (t = 4, 7, 10, 13 for b = 16; 7, 13, 20, 26 for b = 32). At each t:
+    the GPU's table passes the validator (including the threshold
+    invariant), finds are bit-exact against the definitional lookup, find
+    probes equal the oracle's on the GPU's table, negative finds read exactly
+    three buckets, and the GPU's insert reads no more buckets per key than the
+    sequential oracle (reading R17)."""
+    tb, keys, vals = build_table(G, O.IHT, N_SMALL, lf, seed=13, bucket_size=b, threshold=t)
+    st = tb.stats()
+    assert (st["bucket_size"], st["threshold"], st["built"]) == (b, t, 1)
+    T = oracle_view(st, O.IHT, N_SMALL, lf)
+    slots = tb.export()
+    ok, msg = T.validate(keys, vals, slots=slots)
+    assert ok, msg
+    for f in (0.0, 0.5, 1.0):
+        q = W.make_queries(keys, NQ_SMALL, f, seed=19)
+        tb.reset_counters()
+        got = tb.find(q.cuda()).cpu()
+        want = O.lookup(keys, vals, q)
+        assert (O._u32(got) == want).all(), f
+        _, per_query, probes = T.find(q, slots=slots)
+        assert tb.stats()["find_probes"] == probes, f
+        assert (per_query[want == O.EMPTY] == 3).all()  # a miss reads all three buckets
+    S = oracle_view(st, O.IHT, N_SMALL, lf)
+    assert S.build(keys, vals) == 1
+    gpu, cpu = st["insert_probes"] / N_SMALL, S.stats.probes / N_SMALL
+    assert 1.0 <= gpu <= cpu + 0.02, (gpu, cpu)
+
+
+def _keys_with_hashes(consts, m, want, count):
+    """Keys whose (h_0, h_1, h_2) satisfy `want`, found with the oracle's hash."""
+    a, c = consts
+    found = []
+    for k in range(1, 1 << 22):
+        hs = tuple(O.hash_value(a[i], c[i], m, k) for i in range(3))
+        if want(hs, found):
+            found.append((k, hs))
+            if len(found) == count:
+                return found
+    raise AssertionError("no such keys")
+
+
+@pytest.mark.parametrize("max_chain", [1, 4])
+def test_cuckoo1_chain_bound_matches_the_oracle(G, max_chain):
+    """Sec. III-A: an insert fails once the maximum number of exchanges has
+    been made and the next bucket is full. Two keys whose three candidate
+    slots are one and the same slot cannot both be stored: the oracle makes
+    exactly max_chain exchanges and fails; so does the GPU (its last step at
+    the bound only stores into an empty slot). Two keys that share only H_0
+    need one exchange and build under either bound on both sides."""
+    cap, lf, seed = 4, 0.5, 7
+    m = O.num_buckets(cap, lf, 1)
+    consts = O.derive_constants(seed, 0, 3)
+    same = _keys_with_hashes(consts, m, lambda hs, f: len(set(hs)) == 1 and (not f or hs == f[0][1]), 2)
+    apart = _keys_with_hashes(
+        consts, m, lambda hs, f: len(set(hs)) == 3 and (not f or (hs[0] == f[0][1][0] and
+                                                                  not set(hs[1:]) & set(f[0][1]))), 2)
+    for pairs, ok in ((same, False), (apart, True)):
+        keys = np.array([k for k, _ in pairs], np.uint32)
+        vals = keys + np.uint32(100)
+        T = O.Table(O.CUCKOO1, cap, lf, seed=seed, max_chain=max_chain)
+        assert (T.build(keys, vals) == 1) == ok
+        t = G.HashTable("cuckoo1", cap, lf, seed=seed, max_chain=max_chain, max_attempts=1, count_probes=1)
+        kk, vv = torch.from_numpy(keys.view(np.int32)).cuda(), torch.from_numpy(vals.view(np.int32)).cuda()
+        if ok:
+            t.build(kk, vv)
+            assert (O._u32(t.find(kk).cpu()) == vals).all()
+        else:
+            with pytest.raises(G.GhtError) as e:
+                t.build(kk, vv)
+            assert e.value.status == "GHT_ERR_BUILD_FAILED"
+        st = t.stats()
+        assert st["insert_evictions"] == T.stats.evictions, (ok, st["insert_evictions"], T.stats.evictions)
+        assert st["insert_probes"] == T.stats.probes, (ok, st["insert_probes"], T.stats.probes)
+
+
+@pytest.mark.parametrize("scheme,cfg", [("bcht", {}), ("bcht", {"group_build": 1, "ranked_build": 1}),
+                                        ("p2bht", {}), ("bcht_set", {})])
+def test_step_bound_runs_out_and_reports_a_device_timeout(G, scheme, cfg):
+    """Every device loop of a build is bounded. With a per-key bound of one
+    bucket visit, keys that need a second visit (an eviction, a lost CAS,
+    P2BHT's second bucket) stop, the kernel returns, and the build reports
+    GHT_ERR_DEVICE_TIMEOUT without retrying; the table stays unbuilt and the
+    context usable: the same table then builds with the derived bound."""
+    n = 1 << 16
+    keys, vals = W.make_keys(n, 5).cuda(), W.make_values(n, 5).cuda()
+    sets = scheme == "bcht_set"
+    lf = 0.8 if scheme == "p2bht" else 0.99
+    t = G.HashTable(scheme, n, lf, seed=1, max_steps=1, **cfg)
+    with pytest.raises(G.GhtError) as e:
+        t.build(keys, None if sets else vals)
+    assert e.value.status == "GHT_ERR_DEVICE_TIMEOUT"
+    st = t.stats()
+    assert st["built"] == 0 and st["attempts"] == 1
+    with pytest.raises(G.GhtError) as e:
+        t.find(keys)
+    assert e.value.status == "GHT_ERR_NOT_BUILT"
+    u = G.HashTable(scheme, n, lf, seed=1, **cfg)
+    u.build(keys, None if sets else vals)
+    want = torch.ones_like(keys) if sets else vals
+    assert torch.equal(u.find(keys), want)

@@ -15,6 +15,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle as O
 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -44,7 +45,8 @@ def test_no_alloc_find_matches_the_allocating_host_find(G):
     t = G.HashTable("bcht", n, 0.97, seed=5)
     t.build(keys.cuda(), vals.cuda())
     torch.cuda.synchronize()
-    # two calls in a row with different sizes and query mixes
+    # two calls in a row with different sizes and query mixes; the second is
+    # shorter, so stale entries of the first would show in its results
     for call, (nq, frac, seed) in enumerate([((1 << 20) + 3, 0.5, 1), (5000, 0.9, 2)]):
         q = W.make_queries(keys, nq, frac, seed).numpy().view(np.uint32).copy()
         rc_na, out_na = _raw_find(lib, "ght_find_host_noalloc", t._t, q)
@@ -52,9 +54,33 @@ def test_no_alloc_find_matches_the_allocating_host_find(G):
         rc_ref, out_ref = _raw_find(lib, "ght_find_host", t._t, q)
         assert rc_ref == 0, lib.ght_last_error().decode()
         assert np.array_equal(out_na, out_ref), call
-        # and both agree with the inputs for the positive queries
-        hit = out_ref != 0xFFFFFFFF
-        assert hit.sum() >= int(0.99 * frac * nq)
+        # every answer is the value stored with the query's key, or the
+        # sentinel for a key that was not inserted
+        assert np.array_equal(out_na, O.lookup(keys, vals, q)), call
+
+
+def test_no_alloc_find_allocates_nothing_on_the_device(G):
+    """After a first call (and the table's creation, which reserves the
+    staging array), further calls leave the device's free memory unchanged:
+    nothing is allocated from the driver, torch or the library's pool."""
+    lib = G.lib()
+    n = 1 << 18
+    keys, vals = W.make_keys(n, 79), W.make_values(n, 79)
+    t = G.HashTable("bcht", n, 0.9, seed=6)
+    t.build(keys.cuda(), vals.cuda())
+    q = W.make_queries(keys, 1 << 21, 0.5, 3).numpy().view(np.uint32).copy()
+    rc, _ = _raw_find(lib, "ght_find_host_noalloc", t._t, q)
+    assert rc == 0, lib.ght_last_error().decode()
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    reserved_before = torch.cuda.memory_reserved()
+    for _ in range(2):
+        rc, out = _raw_find(lib, "ght_find_host_noalloc", t._t, q)
+        assert rc == 0, lib.ght_last_error().decode()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free_before
+    assert torch.cuda.memory_reserved() == reserved_before
+    assert np.array_equal(out, O.lookup(keys, vals, q))
 
 
 def test_no_alloc_find_rejects_batches_beyond_the_staging_array(G):
