@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ceilings", action="store_true", help="skip the memory-pattern ceiling probe")
+    ap.add_argument("--no-served", action="store_true", help="skip the served-pool record of the default line")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-tables record of the default line")
     ap.add_argument("--tile-lanes", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--build-tile-lanes", type=int, default=0)
@@ -149,10 +151,11 @@ class ClockSampler:
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the find
-# kernel, averaged over its four launches of one step of the default workload,
-# from one ncu capture (profiles/bcht_find_n2e28_traffic.md). It describes the
-# kernel source it was captured from, identified by a hash of the find
-# kernel's headers; after any change to them the traffic is reported as null.
+# kernel, averaged over its four launches of one step of the default workload:
+# one-pass ncu metrics over the recorded step of `bench.py --steps 1 --warmup 1`
+# at 2^28 keys. It describes the kernel source it was captured from,
+# identified by a hash of the find kernel's headers; after any change to them
+# the traffic is reported as null.
 FIND_TRAFFIC = {"bytes_per_launch": 60386213504, "source_sha256_16": "a0ac993b7e41992f",
                "kernel": "bcht_find_async_kernel"}
 
@@ -488,6 +491,14 @@ def run_ours(args, world, rank, local):
                "h2d_gbs_median_min": {k: [round(statistics.median(v), 1), round(min(v), 1)]
                                       for k, v in h2d_gbs.items() if v}}
 
+    # the metric's served-latency clause and the batched path, measured on a
+    # smaller scale beside the headline (rank 0 of a one-GPU run)
+    served = batched = None
+    if rank == 0 and world == 1 and not args.no_served:
+        served = served_measure(dev, SEED + 2, 64, 22, 0.3, build_log2=(20, 22))
+    if rank == 0 and world == 1 and not args.no_batched:
+        batched = batched_measure(dev, SEED + 1, 512, 20, 3, 2)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ns = 1 << 22
@@ -506,7 +517,7 @@ def run_ours(args, world, rank, local):
             "kernels": kernels, "kernel_functions": per_func, "probes_per_key": probes,
             "build_phases_ms": {str(lf): {ph: round(statistics.median(phase_ms[f"{ph}@{lf}"]), 4)
                                          for ph in ("fill", "group", "place", "insert")} for lf in LFS},
-            "pattern_ceilings": ceilings,
+            "pattern_ceilings": ceilings, "served": served, "batched": batched,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -514,22 +525,17 @@ def run_ours(args, world, rank, local):
         dist.destroy_process_group()
 
 
-def run_batched(args, world, rank, local):
-    """512 independent BCHT tables, key counts floor(2^(10 + 12u)), LF ~ U[0.8, 0.99],
-    2 queries per key (50 % positive): one autotuned CUDA-graph launch per step
-    (build + find of every table) against the same tables built and queried with
-    one plain build and one find call each."""
+def batched_measure(dev, seed, num_tables, log2_max, steps, warmup):
+    """Independent BCHT tables, key counts floor(2^(10 + (log2_max - 10) u)),
+    LF ~ U[0.8, 0.99], 2 queries per key (50 % positive): one autotuned
+    CUDA-graph launch per step (build + find of every table) against the same
+    tables built and queried with one plain build and one find call each."""
     import torch
 
     import paper_2108_07232_gb300 as G
     import workloads as W
-    from paper_2108_07232_gb300 import build as B
 
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    B.build()
-    seed = SEED + 1 + rank
-    wk = W.make_batch(512, 10, 22, 0.8, 0.99, 2.0, 0.5, seed, device=dev)
+    wk = W.make_batch(num_tables, 10, log2_max, 0.8, 0.99, 2.0, 0.5, seed, device=dev)
     k, v, q = wk["keys"], wk["values"], wk["queries"]
     ko, qo = wk["key_offsets"], wk["query_offsets"]
     out = torch.empty_like(q)
@@ -538,74 +544,92 @@ def run_batched(args, world, rank, local):
     tuned = b.autotune(k, v, q, out)
     items = int(ko[-1]) + int(qo[-1])
 
-    def timed(fn, steps):
+    def timed(fn, reps):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(steps):
+        for _ in range(reps):
             fn()
         e1.record()
         torch.cuda.synchronize()
         return e0.elapsed_time(e1)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         b.run(k, v, q, out)
-    ms_batched = timed(lambda: b.run(k, v, q, out), args.steps)
+    ms_batched = timed(lambda: b.run(k, v, q, out), steps)
     graph_ms = b.stats()["last_run_ms"]
     ref = out.clone()
     # plain: one table object per table, one build and one find call each
     tables = [G.HashTable("bcht", int(wk["capacities"][t]), float(wk["load_factors"][t]), seed=seed + t)
-              for t in range(512)]
-    sl = [(int(ko[t]), int(ko[t + 1]), int(qo[t]), int(qo[t + 1])) for t in range(512)]
+              for t in range(num_tables)]
+    sl = [(int(ko[t]), int(ko[t + 1]), int(qo[t]), int(qo[t + 1])) for t in range(num_tables)]
 
     def plain():
         for t, (a0, a1, q0, q1) in zip(tables, sl):
             t.build(k[a0:a1], v[a0:a1])
             t.find(q[q0:q1], out[q0:q1])
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         plain()
-    ms_plain = timed(plain, args.steps)
+    ms_plain = timed(plain, steps)
     same = bool(torch.equal(out, ref))
-    value = items * args.steps / (ms_batched / 1e3) / 1e9
-    line = {
-        "metric": "Gkeys/s batched build+find, 512 BCHT tables in one graph launch", "value": round(value, 3),
-        "unit": "Gkeys/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(ms_batched / args.steps, 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "batched_512_bcht_n2^10..2^22_lf0.8..0.99_q2x_f0.5", "tables": 512,
-                   "total_keys": int(ko[-1]), "total_queries": int(qo[-1]), "input_seed": seed},
-        "graph_ms": graph_ms, "autotuned": {kk: tuned[kk] for kk in ("tile_lanes", "keys_per_lane",
-                                                                     "build_tile_lanes", "build_keys_per_lane")},
-        "plain_back_to_back": {"value": round(items * args.steps / (ms_plain / 1e3) / 1e9, 3), "unit": "Gkeys/s",
-                               "ms_per_step": round(ms_plain / args.steps, 3),
-                               "launches_per_step": 512 * 3, "host_syncs_per_step": 512},
+    st = b.stats()
+    b.close()
+    return {
+        "value": round(items * steps / (ms_batched / 1e3) / 1e9, 3), "unit": "Gkeys/s",
+        "ms_per_step": round(ms_batched / steps, 3), "steps": steps, "warmup": warmup,
+        "config": {"workload": f"batched_{num_tables}_bcht_n2^10..2^{log2_max}_lf0.8..0.99_q2x_f0.5",
+                   "tables": num_tables, "total_keys": int(ko[-1]), "total_queries": int(qo[-1]),
+                   "input_seed": seed},
+        "graph_ms": graph_ms, "autotuned": {kk: tuned[kk] for kk in ("tile_lanes", "keys_per_lane", "blocks_per_sm",
+                                                                     "build_tile_lanes", "build_keys_per_lane",
+                                                                     "build_blocks_per_sm") if kk in tuned},
+        "rebuilds": st["rebuilds"],
+        "plain_back_to_back": {"value": round(items * steps / (ms_plain / 1e3) / 1e9, 3), "unit": "Gkeys/s",
+                               "ms_per_step": round(ms_plain / steps, 3),
+                               "launches_per_step": num_tables * 3, "host_syncs_per_step": num_tables},
         "speedup_vs_plain": round(ms_plain / ms_batched, 3), "results_identical": same,
     }
-    print(json.dumps(line), flush=True)
 
 
-def run_served(args, world, rank, local):
-    """128 resident BCHT tables of 2^16..2^24 keys (log-uniform) at LF 0.95 in a
-    pool with a 60 GB budget. A Poisson stream of find batches (sizes
-    log-uniform in [1, 2^20], 70 % positive keys) at 80 % of the pool's
-    measured capacity, plus a build request of a new 2^20..2^24-key table every
-    100 ms, is replayed through the pool (continuous batching) and as serial
-    plain calls; p50/p99 latency and aggregate throughput of both."""
-    import numpy as np
+def run_batched(args, world, rank, local):
+    """512 independent BCHT tables of 2^10..2^22 keys in one graph launch per
+    step against back-to-back plain calls (see batched_measure)."""
     import torch
 
-    import paper_2108_07232_gb300 as G
-    import workloads as W
     from paper_2108_07232_gb300 import build as B
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     B.build()
-    seed = SEED + 2 + rank
+    r = batched_measure(dev, SEED + 1 + rank, 512, 22, args.steps, args.warmup)
+    line = {
+        "metric": "Gkeys/s batched build+find, 512 BCHT tables in one graph launch", "value": r.pop("value"),
+        "unit": r.pop("unit"), "n_gpus": 1, "steps": r.pop("steps"), "warmup": r.pop("warmup"),
+        "ms_per_step": r.pop("ms_per_step"), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": r.pop("config"), **r,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def served_measure(dev, seed, num_tables, log2_max, seconds, build_log2=(20, 24), budget=60 << 30):
+    """num_tables resident BCHT tables of 2^16..2^log2_max keys (log-uniform) at
+    LF 0.95 in a pool with an HBM budget. A Poisson stream of find batches
+    (sizes log-uniform in [1, 2^20], 70 % positive keys) at 80 % of the pool's
+    measured capacity, plus a build request of a new 2^build_log2[0]..
+    2^build_log2[1]-key table every 100 ms, is replayed through the pool
+    (continuous batching) and as serial plain calls; p50/p99 latency and
+    aggregate throughput of both, and whether every answer is the same."""
+    import numpy as np
+    import torch
+
+    import paper_2108_07232_gb300 as G
+    import workloads as W
+
     rng = np.random.default_rng(seed)
-    pool = G.Pool(60 << 30, device=dev)
-    sizes = [int(2 ** (16 + 8 * W.uniform01(t, seed))) for t in range(128)]
+    pool = G.Pool(budget, device=dev)
+    span_log2 = log2_max - 16
+    sizes = [int(2 ** (16 + span_log2 * W.uniform01(t, seed))) for t in range(num_tables)]
     qpool, ids = [], []
     for t, n in enumerate(sizes):
         k, v = W.make_keys(n, seed + t, device=dev), W.make_values(n, seed + t, device=dev)
@@ -619,7 +643,7 @@ def run_served(args, world, rank, local):
         arr = np.cumsum(rng.exponential(1.0 / rate, count)) if rate else np.zeros(count)
         tr = []
         for i in range(count):
-            t = int(rng.integers(0, 128))
+            t = int(rng.integers(0, num_tables))
             size = int(2 ** rng.uniform(0, 20))
             off = int(rng.integers(0, (1 << 20) - size + 1))
             q = qpool[t][off:off + size]
@@ -635,13 +659,14 @@ def run_served(args, world, rank, local):
     capacity_qps = burst_q / mk
     mean_size = burst_q / len(burst)
     rate = 0.8 * capacity_qps / mean_size
-    count = max(100, int(rate * args.served_seconds))
+    count = max(100, int(rate * seconds))
     trace = make_trace(count, rate)
     span = trace[-1]["arrival_s"]
     n_builds = int(span / 0.1)
     builds = []
+    b_lo, b_hi = build_log2
     for j in range(n_builds):
-        n = int(2 ** (20 + 4 * W.uniform01(j, seed ^ 0x62)))
+        n = int(2 ** (b_lo + (b_hi - b_lo) * W.uniform01(j, seed ^ 0x62)))
         k, v = W.make_keys(n, seed + 5000 + j, device=dev), W.make_values(n, seed + 5000 + j, device=dev)
         builds.append({"kind": "build", "keys": k, "values": v, "capacity": n, "load_factor": 0.95,
                        "seed": seed + 5000 + j, "arrival_s": 0.1 * (j + 1)})
@@ -661,20 +686,41 @@ def run_served(args, world, rank, local):
                      "outs": [r["out"] for r in full if r["kind"] == "find"]}
     same = all(torch.equal(a, b) for a, b in zip(out["pool"].pop("outs"), out["serial"].pop("outs")))
     st = pool.stats()
-    line = {
-        "metric": "served p50/p99 find latency and Gkeys/s, 128 resident BCHT tables, continuous batching",
-        "value": out["pool"]["p99_ms"], "unit": "ms (p99 find latency)", "n_gpus": 1, "steps": 1, "warmup": 1,
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "served_128_bcht_n2^16..2^24_lf0.95_budget60GB", "find_requests": count,
-                   "build_requests": n_builds, "arrival_rate_per_s": round(rate, 1),
-                   "offered_load": "0.8 x measured capacity", "mean_find_size": round(mean_size, 1),
-                   "input_seed": seed},
+    pool.close()
+    return {
+        "config": {"workload": f"served_{num_tables}_bcht_n2^16..2^{log2_max}_lf0.95_budget{budget >> 30}GB",
+                   "find_requests": count, "build_requests": n_builds,
+                   "build_keys": f"2^{b_lo}..2^{b_hi} every 100 ms", "arrival_rate_per_s": round(rate, 1),
+                   "trace_s": round(span, 3), "offered_load": "0.8 x measured capacity",
+                   "mean_find_size": round(mean_size, 1), "input_seed": seed},
         "capacity_gqueries_s": round(capacity_qps / 1e9, 3), "pool": out["pool"], "serial_plain_calls": out["serial"],
         "results_identical": same, "mean_requests_per_launch": round(st["mean_requests_per_launch"], 2),
     }
-    pool.close()
+
+
+def run_served(args, world, rank, local):
+    """128 resident tables of 2^16..2^24 keys under a Poisson request stream
+    (see served_measure)."""
+    import torch
+
+    from paper_2108_07232_gb300 import build as B
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+    r = served_measure(dev, SEED + 2 + rank, 128, 24, args.served_seconds)
+    line = {
+        "metric": "served p50/p99 find latency and Gkeys/s, 128 resident BCHT tables, continuous batching",
+        "value": r["pool"]["p99_ms"], "unit": "ms (p99 find latency)", "n_gpus": 1, "steps": 1, "warmup": 1,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        **r,
+    }
     print(json.dumps(line), flush=True)
 
+
+PAPER_IHT_THRESHOLD = {  # (b, t): (insert, positive find) probes at LF 0.86 printed in Sec. VII-A3
+    (16, 4): (2.68, 2.11), (16, 7): (2.29, 1.86), (16, 10): (1.89, 1.6), (16, 13): (1.49, 1.33),
+}
 
 PAPER_PROBES = {  # (scheme, lf): (insert, find_pos, find_neg) printed in Sec. VII (50M keys, TITAN V)
     ("bcht", 0.9): (1.11, None, None), ("bcht", 0.99): (1.43, 1.38, 2.80),
@@ -759,6 +805,15 @@ def run_sweep(args, world, rank, local):
         rows.append({"config": "b32_n2^24", **measure_table(scheme, n, lf, (0.0, 1.0), SEED + 13, dev, **cfg)})
     for lf in (0.9, 0.99):
         rows.append({"config": "keys_only_set_n2^24", **measure_table("bcht_set", n, lf, (0.0, 0.5, 1.0), SEED + 14, dev)})
+    # Sec. VII-A3: IHT thresholds at 20/40/60/80 % of b (t = 4, 7, 10, 13 for
+    # b = 16 at LF 0.86, where the paper prints insert and positive-find
+    # probes; t = 7, 13, 20, 26 for b = 32 at LF 0.9)
+    for b, lf, ts in ((16, 0.86, (4, 7, 10, 13)), (32, 0.9, (7, 13, 20, 26))):
+        for t in ts:
+            r = measure_table("iht", n, lf, (0.0, 1.0), SEED + 15, dev, bucket_size=b, threshold=t)
+            if (b, t) in PAPER_IHT_THRESHOLD:
+                r["paper_probes_insert_pos"] = PAPER_IHT_THRESHOLD[(b, t)]
+            rows.append({"config": "iht_threshold_sweep_n2^24", **r})
     print(json.dumps({"metric": "scheme sweep: build/find Gkeys/s and probes per key", "workload": "sweep",
                       "rows": rows}), flush=True)
 

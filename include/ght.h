@@ -101,7 +101,8 @@ typedef struct {
    * range (H_0(k) >> s), so the build's concurrent stores and atomics stay in
    * a few MB of the table at a time. 1 = on, -1 = off, 0 = default: on for
    * BCHT and BCHT_SET tables of at least 4x the device's L2 size. Needs
-   * scratch (ght_build_scratch_bytes), else the build runs in input order. */
+   * scratch (ght_build_scratch_bytes) and 16-byte aligned key and value
+   * arrays, else the build runs in input order. */
   int32_t group_build;
   /* Two-phase build of BCHT and BCHT_SET: every key that arrives at its
    * first-choice bucket while it has room is stored at its arrival rank
@@ -327,6 +328,8 @@ typedef struct {
   int32_t build_tile_lanes, build_keys_per_lane;  /* insert shape */
   double last_run_ms;          /* device time of the last ght_batch_run graph launch */
   uint64_t graph_launches;
+  int32_t blocks_per_sm;       /* find grid: resident blocks per SM (0 = as many as fit) */
+  int32_t build_blocks_per_sm; /* insert grid, likewise */
 } ght_batch_stats_t;
 
 /* Create num_tables empty tables, table t sized for h_capacities[t] keys at
@@ -359,9 +362,10 @@ int ght_batch_find(const ght_batch *b, const uint32_t *d_queries, uint32_t *d_ou
 int ght_batch_run(ght_batch *b, const uint32_t *d_keys, const uint32_t *d_values, const uint32_t *d_queries,
                   uint32_t *d_out);
 
-/* Choose the insert and find launch shapes (lanes per bucket tile, keys per
- * lane) by timing each candidate on these arrays; keeps the fastest. The
- * tables are rebuilt as a side effect. */
+/* Choose the insert and find launch shapes by timing each candidate on
+ * these arrays: first the tile shape (lanes per bucket tile, keys per lane),
+ * then the grid (1-4 resident blocks per SM, or as many as fit) of the best
+ * shape; keeps the fastest. The tables are rebuilt as a side effect. */
 int ght_batch_autotune(ght_batch *b, const uint32_t *d_keys, const uint32_t *d_values,
                        const uint32_t *d_queries, uint32_t *d_out);
 

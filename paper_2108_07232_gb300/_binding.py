@@ -73,6 +73,7 @@ class GhtBatchStats(C.Structure):
         ("rebuilds", C.c_uint32), ("tuned", C.c_int32), ("tile_lanes", C.c_int32),
         ("keys_per_lane", C.c_int32), ("build_tile_lanes", C.c_int32), ("build_keys_per_lane", C.c_int32),
         ("last_run_ms", C.c_double), ("graph_launches", C.c_uint64),
+        ("blocks_per_sm", C.c_int32), ("build_blocks_per_sm", C.c_int32),
     ]
 
     def as_dict(self) -> dict:

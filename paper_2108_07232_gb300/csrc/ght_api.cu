@@ -476,6 +476,11 @@ int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n,
   t->n_stored = 0;
   bool ranked = wants_ranked(t, n);
   bool grouped = wants_grouping(t, n);
+  if (grouped && ((reinterpret_cast<uintptr_t>(k) | reinterpret_cast<uintptr_t>(v ? v : k)) & 15u)) {
+    // the grouping copies 16-byte pieces of the input: unaligned arrays build ungrouped
+    grouped = false;
+    ranked = t->shape.ranked_build > 0;
+  }
   void *pool_buf = nullptr;
   char *scr = nullptr;
   if (ranked || grouped) {

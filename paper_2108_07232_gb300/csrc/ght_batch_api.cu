@@ -68,7 +68,8 @@ struct ght_batch {
   }
 
   int shape_sig() const {
-    return build_o.tile_lanes * 1000 + build_o.keys_per_lane * 100 + find_o.tile_lanes * 10 + find_o.keys_per_lane;
+    return ((build_o.blocks_per_sm * 64 + find_o.blocks_per_sm) * 100 + build_o.tile_lanes) * 1000 +
+           build_o.keys_per_lane * 100 + find_o.tile_lanes * 10 + find_o.keys_per_lane;
   }
 
   void drop_graph() {
@@ -392,25 +393,58 @@ int ght_batch_autotune(ght_batch *b, const uint32_t *d_keys, const uint32_t *d_v
                        uint32_t *d_out) {
   int rc = check_ready(b);
   if (rc) return rc;
+  // tile shapes (lanes per bucket, keys per lane), then the grid (resident
+  // blocks per SM; 0 = as many as fit) of the chosen shape
   static const int kBuild[][2] = {{16, 1}, {8, 1}, {8, 2}, {4, 2}};
   static const int kFind[][2] = {{4, 2}, {4, 1}, {8, 2}, {8, 1}, {16, 1}};
+  static const int kGrid[] = {0, 1, 2, 3, 4};
+  if (b->build_o.blocks_per_sm < 0 || b->find_o.blocks_per_sm < 0) return fail(GHT_ERR_INVALID_ARG, "negative grid");
   auto time_between = [&](float *out_ms) -> int {
     const cudaError_t e = cudaEventSynchronize(b->ev1);
     if (e != cudaSuccess) return cuda_fail(e, "timing a candidate");
     return cudaEventElapsedTime(out_ms, b->ev0, b->ev1) == cudaSuccess ? GHT_OK : fail(GHT_ERR_CUDA, "event timing");
   };
-  float best = 3.0e38f;
+  auto time_build = [&](float *total) -> int {
+    *total = 0.f;
+    for (int rep = 0; rep < 3; ++rep) {
+      int r = ght_batch_build(b, d_keys, d_values);
+      if (r) return r;
+      float ms = 0.f;
+      if ((r = time_between(&ms))) return r;
+      if (rep > 0) *total += ms;  // the first repetition warms up
+    }
+    return GHT_OK;
+  };
+  auto time_find = [&](float *total) -> int {
+    *total = 0.f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(b->ev0, b->stream);
+      int r = launch_find(b, 0, b->T, d_queries, d_out);
+      if (r) return r;
+      cudaEventRecord(b->ev1, b->stream);
+      float ms = 0.f;
+      if ((r = time_between(&ms))) return r;
+      if (rep > 0) *total += ms;
+    }
+    return GHT_OK;
+  };
+  float best = 3.0e38f, total = 0.f;
   ght::LaunchOpts best_o = b->build_o;
+  b->build_o.blocks_per_sm = 0;
   for (const auto &c : kBuild) {
     b->build_o.tile_lanes = c[0];
     b->build_o.keys_per_lane = c[1];
-    float total = 0.f;
-    for (int rep = 0; rep < 3; ++rep) {
-      if ((rc = ght_batch_build(b, d_keys, d_values))) return rc;
-      float ms = 0.f;
-      if ((rc = time_between(&ms))) return rc;
-      if (rep > 0) total += ms;  // the first repetition warms up
+    if ((rc = time_build(&total))) return rc;
+    if (total < best) {
+      best = total;
+      best_o = b->build_o;
     }
+  }
+  for (int g : kGrid) {
+    if (g == 0) continue;  // measured with the shapes
+    b->build_o = best_o;
+    b->build_o.blocks_per_sm = g;
+    if ((rc = time_build(&total))) return rc;
     if (total < best) {
       best = total;
       best_o = b->build_o;
@@ -420,18 +454,21 @@ int ght_batch_autotune(ght_batch *b, const uint32_t *d_keys, const uint32_t *d_v
   if ((rc = ght_batch_build(b, d_keys, d_values))) return rc;
   best = 3.0e38f;
   best_o = b->find_o;
+  b->find_o.blocks_per_sm = 0;
   for (const auto &c : kFind) {
     b->find_o.tile_lanes = c[0];
     b->find_o.keys_per_lane = c[1];
-    float total = 0.f;
-    for (int rep = 0; rep < 3; ++rep) {
-      cudaEventRecord(b->ev0, b->stream);
-      if ((rc = launch_find(b, 0, b->T, d_queries, d_out))) return rc;
-      cudaEventRecord(b->ev1, b->stream);
-      float ms = 0.f;
-      if ((rc = time_between(&ms))) return rc;
-      if (rep > 0) total += ms;
+    if ((rc = time_find(&total))) return rc;
+    if (total < best) {
+      best = total;
+      best_o = b->find_o;
     }
+  }
+  for (int g : kGrid) {
+    if (g == 0) continue;
+    b->find_o = best_o;
+    b->find_o.blocks_per_sm = g;
+    if ((rc = time_find(&total))) return rc;
     if (total < best) {
       best = total;
       best_o = b->find_o;
@@ -460,6 +497,8 @@ int ght_batch_stats(const ght_batch *b, ght_batch_stats_t *out) {
   out->build_keys_per_lane = b->build_o.keys_per_lane;
   out->last_run_ms = b->last_run_ms;
   out->graph_launches = b->graph_launches;
+  out->blocks_per_sm = b->find_o.blocks_per_sm;
+  out->build_blocks_per_sm = b->build_o.blocks_per_sm;
   return GHT_OK;
 }
 

@@ -7,6 +7,7 @@
 // plus a partial-line write-back. Grouping the pairs by H_0(k) >> shift and
 // inserting the groups in order keeps the in-flight inserts inside a window
 // of a few MB of the table, whose lines then stay in L2 while they fill up.
+#include "ght_bulk.cuh"
 #include "ght_internal.h"
 #include "ght_kernels.cuh"
 
@@ -17,7 +18,8 @@ __device__ __forceinline__ uint32_t group_of(const TableView &tv, uint32_t k, in
 }
 
 // Pass 1: per-group counts (block-local histogram in shared memory). With
-// 16-byte aligned keys each thread takes four keys per 16-byte load.
+// 16-byte aligned keys each thread takes four keys per 16-byte load, two
+// loads in flight per turn.
 __global__ void __launch_bounds__(256)
 group_count_kernel(TableView tv, const uint32_t *__restrict__ keys, uint64_t n, int shift, uint32_t groups,
                    uint32_t *__restrict__ counts) {
@@ -29,14 +31,17 @@ group_count_kernel(TableView tv, const uint32_t *__restrict__ keys, uint64_t n, 
   if ((reinterpret_cast<uintptr_t>(keys) & 15u) == 0u) {
     const uint4 *k4 = reinterpret_cast<const uint4 *>(keys);
     const uint64_t n4 = n / 4;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
-      const uint4 k = __ldg(k4 + i);
-      const uint32_t g0 = group_of(tv, k.x, shift), g1 = group_of(tv, k.y, shift);
-      const uint32_t g2 = group_of(tv, k.z, shift), g3 = group_of(tv, k.w, shift);
-      atomicAdd(&sh[g0], 1u);
-      atomicAdd(&sh[g1], 1u);
-      atomicAdd(&sh[g2], 1u);
-      atomicAdd(&sh[g3], 1u);
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += 2 * stride) {
+      const bool second = i + stride < n4;
+      const uint4 ka = __ldg(k4 + i);
+      const uint4 kb = second ? __ldg(k4 + i + stride) : ka;
+      const uint32_t a[4] = {ka.x, ka.y, ka.z, ka.w}, b[4] = {kb.x, kb.y, kb.z, kb.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) atomicAdd(&sh[group_of(tv, a[j], shift)], 1u);
+      if (second) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) atomicAdd(&sh[group_of(tv, b[j], shift)], 1u);
+      }
     }
     head = n4 * 4;
   }
@@ -84,52 +89,99 @@ group_scan_kernel(const uint32_t *__restrict__ counts, uint32_t groups, uint32_t
   }
 }
 
-// Pass 2: scatter pairs to their group. Each block takes a tile of
-// kGroupTile pairs, ranks them per group in shared memory, reserves one
-// output range per non-empty group with a single global atomic, orders the
-// tile by group in shared memory, and then writes it with consecutive
-// threads storing consecutive items, so a group's items leave as one
-// contiguous run instead of scattered 4-byte stores.
-constexpr int kGroupPerThread = 16;
-constexpr int kGroupTile = 256 * kGroupPerThread;
+// Pass 2: scatter pairs to their group. Each block takes tiles of
+// kGroupTile pairs; a tile's keys and values arrive in shared memory by bulk
+// asynchronous copies issued one tile ahead (two buffers, each completed on
+// its own mbarrier), so the copies of tile i + 1 run while tile i is ranked
+// per group, reordered by group in place, and written out. One output range
+// per non-empty group is reserved with a single global atomic, and
+// consecutive threads store consecutive items, so a group's items leave as
+// one contiguous run instead of scattered 4-byte stores. Keys and values
+// must be 16-byte aligned (the host checks); a tile's last n mod 4 items are
+// read directly.
+constexpr int kGroupThreads = 256;
+constexpr int kGroupPerThread = 15;  // 3840-pair tiles: 70 KB of shared memory, three blocks per SM
+constexpr int kGroupTile = kGroupThreads * kGroupPerThread;
+constexpr uint32_t kGroupWaitPolls = 1u << 26;  // bounded wait for a tile's copies
 
-// Compiled for 4 resident blocks per SM (64 registers, a few spilled; the
-// shared memory, 46 KB per block at 512 groups, allows 4): the pass is
-// latency-bound between its barriers, so resident blocks are what count
-// (2.65 ms at 2^28 pairs against 3.43 ms at the compiler's 2 blocks).
-__global__ void __launch_bounds__(256, 4)
+// shared memory of the scatter: two tile buffers (keys, values), the group
+// of each reordered item, and per-group count, prefix and reserved position
+size_t group_scatter_smem(uint32_t groups) {
+  return 4ull * kGroupTile * sizeof(uint32_t) + kGroupTile * sizeof(uint16_t) + 3ull * groups * sizeof(uint32_t);
+}
+
+__global__ void __launch_bounds__(kGroupThreads, 3)
 group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint32_t *__restrict__ values,
                      uint64_t n, int shift, uint32_t groups, uint32_t *__restrict__ cursors,
                      uint32_t *__restrict__ out_k, uint32_t *__restrict__ out_v) {
-  extern __shared__ uint32_t sh[];
-  uint32_t *cnt = sh;                    // [groups] items of each group in the tile
-  uint32_t *pre = cnt + groups;          // [groups] exclusive prefix of cnt
-  uint32_t *base = pre + groups;         // [groups] reserved output position
-  uint32_t *sk = base + groups;          // [kGroupTile] tile keys ordered by group
-  uint32_t *sv = sk + kGroupTile;        // [kGroupTile] tile values
-  uint16_t *sg = reinterpret_cast<uint16_t *>(sv + kGroupTile);  // [kGroupTile] group of each ordered item
-  __shared__ uint32_t warp_sums[8];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (uint64_t t0 = (uint64_t)blockIdx.x * kGroupTile; t0 < n; t0 += (uint64_t)gridDim.x * kGroupTile) {
-    const uint32_t tile_n = (uint32_t)(n - t0 < (uint64_t)kGroupTile ? n - t0 : (uint64_t)kGroupTile);
-    for (uint32_t i = threadIdx.x; i < groups; i += blockDim.x) cnt[i] = 0u;
+  extern __shared__ uint4 gs_smem[];
+  uint32_t *bufs = reinterpret_cast<uint32_t *>(gs_smem);  // [2][keys kGroupTile | values kGroupTile]
+  uint16_t *gid = reinterpret_cast<uint16_t *>(bufs + 4 * kGroupTile);  // [kGroupTile] group of each reordered item
+  uint32_t *cnt = reinterpret_cast<uint32_t *>(gid + kGroupTile);      // [groups] items of each group in the tile
+  uint32_t *pre = cnt + groups;                                           // [groups] exclusive prefix of cnt
+  uint32_t *base = pre + groups;                                          // [groups] reserved output position
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ uint32_t warp_sums[kGroupThreads / 32];
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint64_t ntiles = (n + kGroupTile - 1) / kGroupTile;
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    mbar_init_fence();
+    s_abort = 0;
+  }
+  __syncthreads();
+  // thread 0: copy the whole 16-byte pieces of tile `tile` into buffer b
+  auto issue = [&](uint64_t tile, int b) {
+    const uint64_t t0 = tile * kGroupTile;
+    const uint32_t tn = (uint32_t)(n - t0 < (uint64_t)kGroupTile ? n - t0 : (uint64_t)kGroupTile);
+    const uint32_t bytes = (tn / 4u) * 16u;
+    uint32_t *dk = bufs + 2 * b * kGroupTile;
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&bars[b], 2u * bytes);
+    if (bytes) {
+      bulk_g2s(dk, keys + t0, bytes, &bars[b]);
+      bulk_g2s(dk + kGroupTile, values + t0, bytes, &bars[b]);
+    }
+  };
+  uint32_t j = 0;  // this block's tile count so far
+  uint64_t tile = blockIdx.x;
+  if (tid == 0 && tile < ntiles) issue(tile, 0);
+  for (; tile < ntiles; tile += gridDim.x, ++j) {
+    const int b = (int)(j & 1u);
+    const uint64_t next = tile + gridDim.x;
+    if (tid == 0 && next < ntiles) issue(next, b ^ 1);  // buffer b ^ 1 was released at the end of the last tile
+    for (uint32_t i = tid; i < groups; i += kGroupThreads) cnt[i] = 0u;
+    if (!mbar_wait_bounded(&bars[b], (j >> 1) & 1u, kGroupWaitPolls)) s_abort = 1;
     __syncthreads();
-    uint32_t k[kGroupPerThread], v[kGroupPerThread], g[kGroupPerThread], rank[kGroupPerThread];
+    if (s_abort) {
+      if (tid == 0) {
+        atomicOr(&tv.ctrl->status, kStatusTimeout);
+        if (next < ntiles) mbar_wait_bounded(&bars[b ^ 1], ((j + 1) >> 1) & 1u, kGroupWaitPolls);
+      }
+      return;
+    }
+    const uint64_t t0 = tile * kGroupTile;
+    const uint32_t tn = (uint32_t)(n - t0 < (uint64_t)kGroupTile ? n - t0 : (uint64_t)kGroupTile);
+    const uint32_t tbulk = tn & ~3u;  // items that came by the bulk copies
+    uint32_t *sk = bufs + 2 * b * kGroupTile, *sv = sk + kGroupTile;
+    uint32_t k[kGroupPerThread], v[kGroupPerThread], gr[kGroupPerThread];
 #pragma unroll
     for (int u = 0; u < kGroupPerThread; ++u) {
-      const uint32_t i = (uint32_t)u * blockDim.x + threadIdx.x;  // coalesced reads
-      if (i < tile_n) {
-        k[u] = __ldg(keys + t0 + i);
-        v[u] = __ldg(values + t0 + i);
-        g[u] = group_of(tv, k[u], shift);
-        rank[u] = atomicAdd(&cnt[g[u]], 1u);
+      const uint32_t i = (uint32_t)u * kGroupThreads + tid;
+      if (i < tn) {
+        k[u] = i < tbulk ? sk[i] : __ldg(keys + t0 + i);
+        v[u] = i < tbulk ? sv[i] : __ldg(values + t0 + i);
+        const uint32_t g = group_of(tv, k[u], shift);
+        gr[u] = (g << 16) | atomicAdd(&cnt[g], 1u);  // group < 4096, rank < kGroupTile
       }
     }
     __syncthreads();
     // exclusive prefix over the groups (each thread a contiguous run of them)
     // and one output reservation per non-empty group
-    const uint32_t per = (groups + blockDim.x - 1) / blockDim.x;
-    const uint32_t g0 = threadIdx.x * per, g1 = g0 + per < groups ? g0 + per : groups;
+    const uint32_t per = (groups + kGroupThreads - 1) / kGroupThreads;
+    const uint32_t g0 = tid * per, g1 = g0 + per < groups ? g0 + per : groups;
     uint32_t run = 0;
     for (uint32_t i = g0; i < g1; ++i) run += cnt[i];
     uint32_t incl = run;
@@ -143,26 +195,43 @@ group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint
     uint32_t before = 0;
     for (int w = 0; w < wid; ++w) before += warp_sums[w];
     uint32_t acc = before + incl - run;
-    for (uint32_t i = g0; i < g1; ++i) {
-      pre[i] = acc;
-      acc += cnt[i];
-      if (cnt[i]) base[i] = atomicAdd(&cursors[i], cnt[i]);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < kGroupPerThread; ++u) {
-      const uint32_t i = (uint32_t)u * blockDim.x + threadIdx.x;
-      if (i < tile_n) {
-        const uint32_t at = pre[g[u]] + rank[u];
-        sk[at] = k[u];
-        sv[at] = v[u];
-        sg[at] = (uint16_t)g[u];
+    // reservations: with at most two groups per thread the atomics' results
+    // stay in registers until after the reorder, so their round trip overlaps it
+    uint32_t r0 = 0u, r1 = 0u;
+    if (per <= 2) {
+      const uint32_t c0 = g0 < g1 ? cnt[g0] : 0u, c1 = g0 + 1 < g1 ? cnt[g0 + 1] : 0u;
+      if (c0) r0 = atomicAdd(&cursors[g0], c0);
+      if (c1) r1 = atomicAdd(&cursors[g0 + 1], c1);
+      if (g0 < g1) pre[g0] = acc;
+      if (g0 + 1 < g1) pre[g0 + 1] = acc + c0;
+    } else {
+      for (uint32_t i = g0; i < g1; ++i) {
+        pre[i] = acc;
+        acc += cnt[i];
+        if (cnt[i]) base[i] = atomicAdd(&cursors[i], cnt[i]);
       }
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < tile_n; i += blockDim.x) {
-      const uint32_t gi = sg[i];
-      const uint32_t at = base[gi] + (i - pre[gi]);
+    // reorder by group in place (every item of the buffer was read above)
+#pragma unroll
+    for (int u = 0; u < kGroupPerThread; ++u) {
+      const uint32_t i = (uint32_t)u * kGroupThreads + tid;
+      if (i < tn) {
+        const uint32_t g = gr[u] >> 16;
+        const uint32_t at = pre[g] + (gr[u] & 0xFFFFu);
+        sk[at] = k[u];
+        sv[at] = v[u];
+        gid[at] = (uint16_t)g;
+      }
+    }
+    if (per <= 2) {
+      if (g0 < g1) base[g0] = r0;
+      if (g0 + 1 < g1) base[g0 + 1] = r1;
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < tn; i += kGroupThreads) {
+      const uint32_t g = gid[i];
+      const uint32_t at = base[g] + (i - pre[g]);
       out_k[at] = sk[i];
       out_v[at] = sv[i];
     }
@@ -175,6 +244,7 @@ cudaError_t launch_group(const TableView &tv, const uint32_t *keys, const uint32
                          uint32_t *out_v, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   if (n > 0xFFFFFFFFull || groups == 0 || groups > kMaxGroups) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(values)) & 15u) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(counts, 0, groups * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   int blocks = 0;
@@ -185,11 +255,10 @@ cudaError_t launch_group(const TableView &tv, const uint32_t *keys, const uint32
   group_scan_kernel<<<1, 1024, 0, s>>>(counts, groups, cursors);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const uint64_t tiles = (n + kGroupTile - 1) / kGroupTile;
-  const size_t smem = 3ull * groups * sizeof(uint32_t) + 2ull * kGroupTile * sizeof(uint32_t) +
-                      kGroupTile * sizeof(uint16_t);
-  e = grid_for_smem(group_scatter_kernel, 256, smem, tiles * 256, 0, &blocks);
+  const size_t smem = group_scatter_smem(groups);
+  e = grid_for_smem(group_scatter_kernel, kGroupThreads, smem, tiles * kGroupThreads, 0, &blocks);
   if (e != cudaSuccess) return e;
-  group_scatter_kernel<<<blocks, 256, smem, s>>>(tv, keys, values, n, shift, groups, cursors, out_k, out_v);
+  group_scatter_kernel<<<blocks, kGroupThreads, smem, s>>>(tv, keys, values, n, shift, groups, cursors, out_k, out_v);
   return cudaGetLastError();
 }
 

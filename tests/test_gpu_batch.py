@@ -73,8 +73,16 @@ def test_batch_plain_and_autotuned_paths_agree(G, work):
     _check_tables(G, b, work, out)
     tuned = b.autotune(k, v, q)
     assert tuned["tuned"] == 1
+    # the search covers the grid as well as the tile shape
+    assert tuned["blocks_per_sm"] in (0, 1, 2, 3, 4) and tuned["build_blocks_per_sm"] in (0, 1, 2, 3, 4)
     out2 = b.run(k, v, q)
     _check_tables(G, b, work, out2, validate=False)
+    # every grid of the search answers the same
+    for grid in (1, 4):
+        c = G.Batch(work["capacities"], work["load_factors"], seed=4, blocks_per_sm=grid, build_blocks_per_sm=grid)
+        c.set_layout(work["key_offsets"], work["query_offsets"])
+        assert c.stats()["blocks_per_sm"] == grid
+        _check_tables(G, c, work, c.run(k, v, q), validate=False)
 
 
 def test_batch_edge_cases(G):

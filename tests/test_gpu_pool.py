@@ -131,3 +131,53 @@ def test_pool_replay_pool_and_serial(G, tables):
     for a, b in zip(outs["pool"], outs["serial"]):
         assert torch.equal(a, b)
     pool.close()
+
+
+def test_pool_finds_exact_while_builds_are_admitted(G, tables):
+    """Builds of new tables are admitted and run on the build worker's
+    stream while find launches are in flight: every find answer is the same
+    as when it ran alone and equals the definitional lookup, and finds
+    submitted on a new table before its build completed wait for it and
+    answer from it."""
+    pool = G.Pool(1 << 30)
+    ids = []
+    for i, (n, k, v) in enumerate(tables):
+        tk, tid = pool.submit_build(n, 0.95, 60 + i, k, v)
+        assert pool.wait(tk)["status"] == 0
+        ids.append(tid)
+    reqs = _requests(tables, 240, seed=5)
+    alone = []
+    for t, q in reqs:
+        out = torch.full_like(q, 3)
+        pool.wait(pool.submit_find(ids[t], q, out))
+        alone.append(out)
+    fresh = []
+    for j, n in enumerate((200000, 50000, 1000)):
+        k, v = W.make_keys(n, 300 + j), W.make_values(n, 300 + j)
+        fresh.append((n, k.cuda(), v.cuda(), k, v))
+    mixed, tickets, new_finds = [], [], []
+    builds = []
+    for i, (t, q) in enumerate(reqs):
+        if i % 80 == 0:  # a build request arrives among the finds
+            n, dk, dv, hk, hv = fresh[i // 80]
+            btk, bid = pool.submit_build(n, 0.9, 400 + i, dk, dv)
+            builds.append(btk)
+            nq = W.make_queries(hk, 20000, 0.5, seed=500 + i).cuda()
+            nout = torch.full_like(nq, 11)
+            new_finds.append((pool.submit_find(bid, nq, nout), nq, nout, hk, hv))
+        out = torch.full_like(q, 5)
+        tickets.append(pool.submit_find(ids[t], q, out))
+        mixed.append(out)
+    for tk in tickets:
+        assert pool.wait(tk, timeout=120)["status"] == 0
+    for btk in builds:
+        assert pool.wait(btk, timeout=120)["status"] == 0
+    assert pool.stats()["builds_done"] >= len(tables) + len(builds)
+    for (t, q), a, m in zip(reqs, alone, mixed):
+        assert torch.equal(a, m)
+        n, k, v = tables[t]
+        assert (O._u32(m.cpu()) == O.lookup(k.cpu(), v.cpu(), q.cpu())).all()
+    for ftk, nq, nout, hk, hv in new_finds:
+        assert pool.wait(ftk, timeout=120)["status"] == 0
+        assert (O._u32(nout.cpu()) == O.lookup(hk, hv, nq.cpu())).all()
+    pool.close()

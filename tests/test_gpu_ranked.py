@@ -153,3 +153,46 @@ def test_no_scratch_means_cuckoo_insert_of_every_key(G):
         assert (O._u32(out.cpu()) == O.lookup(keys, vals, q.cpu())).all()
     finally:
         G.ght_destroy(h)
+
+
+def test_grouped_build_with_one_crowded_bucket_over_stale_slots(G):
+    """The grouped two-phase build with 2,500 of 20,000 keys sharing one
+    first-choice bucket (a long overflow run from one place) over a table
+    that already holds another build's pairs: the result must pass the
+    validator with bit-exact finds, and the crowded bucket's keys beyond its
+    16 slots all reach the overflow list."""
+    n, lf, seed = 20000, 0.5, 31
+    m = O.num_buckets(n, lf, 16)
+    a, c = O.derive_constants(seed, 0, 3)
+    cand = np.arange(1, 1 << 24, dtype=np.uint64)
+    h0 = ((np.uint64(a[0]) * cand + np.uint64(c[0])) % np.uint64(O.PRIME)) % np.uint64(m)
+    same = cand[h0 == h0[0]][:2500].astype(np.uint32)
+    assert same.size == 2500
+    rest = W.make_keys(3 * n, 96).numpy().view(np.uint32)
+    rest = rest[~np.isin(rest, same)][: n - same.size]
+    keys = torch.from_numpy(np.concatenate([same, rest]).view(np.int32).copy())
+    vals = W.make_values(n, 96)
+    t = G.HashTable("bcht", n, lf, seed=seed, count_probes=1, group_build=1)
+    other_k, other_v = W.make_keys(n, 97), W.make_values(n, 97)
+    t.build(other_k.cuda(), other_v.cuda())  # stale contents under the next build
+    t.build(keys.cuda(), vals.cuda())
+    st = _check(t, O.BCHT, keys, vals, n, lf, 16)
+    assert st["attempts"] == 1 and st["last_build_grouped"] == 1 and st["last_build_ranked"] == 1
+    assert st["place_overflow"] >= 2500 - 16
+
+
+def test_unaligned_arrays_build_ungrouped(G):
+    """The grouping pass copies 16-byte pieces of the input; key and value
+    arrays that start off a 16-byte boundary build without it, with the
+    same results."""
+    n = 30001
+    keys, vals = W.make_keys(n + 1, 98), W.make_values(n + 1, 98)
+    dk, dv = keys.cuda(), vals.cuda()
+    t = G.HashTable("bcht", n, 0.95, seed=3, group_build=1)
+    t.build(dk[1:], dv[1:])  # 4 bytes past a 16-byte boundary
+    st = t.stats()
+    assert st["built"] == 1 and st["last_build_grouped"] == 0
+    q = W.make_queries(keys[1:], n, 0.5, seed=2)
+    assert (O._u32(t.find(q.cuda()).cpu()) == O.lookup(keys[1:], vals[1:], q)).all()
+    t.build(dk[:n], dv[:n])  # aligned again: grouped
+    assert t.stats()["last_build_grouped"] == 1
