@@ -59,6 +59,8 @@ def parse():
                     help="hbm: 2^28-key BCHT tables (default); batched: 512 uneven tables in one graph "
                          "launch; served: a table pool under Poisson request arrivals")
     ap.add_argument("--served-seconds", type=float, default=1.0, help="served: length of the arrival trace")
+    ap.add_argument("--sharded", action="store_true",
+                    help="one table sharded over the ranks (partition hash + all-to-all) instead of a table per rank")
     return ap.parse_args()
 
 
@@ -525,6 +527,80 @@ def run_ours(args, world, rank, local):
         dist.destroy_process_group()
 
 
+def run_sharded(args, world, rank, local):
+    """One table sharded over the ranks (paper_2108_07232_gb300.sharded): each
+    rank holds 2^log2n pairs and queries of its own; per step a table of all
+    ranks' pairs is built at LF 0.99 and at 0.9 (partition by the partition
+    hash, all-to-all, shard build) and each rank's 2^log2n positive and
+    2^log2n negative queries are found (partition, all-to-all, shard find,
+    reverse all-to-all, return to query order). Weak scaling: per-rank work is
+    fixed as ranks are added."""
+    import torch
+    import torch.distributed as dist
+
+    import workloads as W
+    from paper_2108_07232_gb300 import build as B
+    from paper_2108_07232_gb300.sharded import ShardedTable
+
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or not os.path.exists(B.LIB):
+        B.build()
+    if world > 1:
+        dist.barrier()
+    n = 1 << args.log2n
+    seed = rank_seed(SEED, rank)
+    keys = W.make_keys(n, seed, device=dev)
+    vals = W.make_values(n, seed, device=dev)
+    pos = W.make_queries(keys, n, 1.0, seed)
+    neg = W.make_negatives(n, n, seed, device=dev)
+    tables = {lf: ShardedTable("bcht", world * n, lf, seed=SEED) for lf in LFS}
+
+    def step():
+        for lf in LFS:
+            t = tables[lf]
+            t.build(keys, vals)
+            t.find(pos)
+            t.find(neg)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        step()
+    ev1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = reduce_max(ev0.elapsed_time(ev1), world, dev)
+    value = whole_job_value(len(LFS) * 3 * n, args.steps, world, ms)
+    shard = {str(lf): tables[lf].n_local for lf in LFS}
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": round(value, 3), "unit": "Gkeys/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"bcht_b16_h3_sharded_one_table_{world}x2^{args.log2n}_lf0.99+0.9_find_pos+neg",
+                       "keys_per_rank": n, "load_factors": list(LFS), "exchange": "nccl all-to-all" if world > 1 else
+                       "none (one rank: partition and the local shard only)",
+                       "l2": "inputs larger than L2", "input_seed": SEED},
+            "shard_keys_rank0": shard, "clocks": clocks,
+        }), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def batched_measure(dev, seed, num_tables, log2_max, steps, warmup):
     """Independent BCHT tables, key counts floor(2^(10 + (log2_max - 10) u)),
     LF ~ U[0.8, 0.99], 2 queries per key (50 % positive): one autotuned
@@ -907,6 +983,9 @@ def main():
         return
     if args.workload == "sizes":
         run_sizes(args, world, rank, local)
+        return
+    if args.sharded:
+        run_sharded(args, world, rank, local)
         return
     run_ours(args, world, rank, local)
 

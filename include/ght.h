@@ -252,6 +252,40 @@ int ght_find_host(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out
 #define GHT_NOALLOC_MAX_QUERIES (1u << 22)
 int ght_find_host_noalloc(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out, uint64_t n);
 
+/* ---------------------------------------------------------------------------
+ * Sharding one table over G GPUs (one rank each). The paper's tables live on
+ * one GPU; they shard by key: a partition hash g(k) = ((a_g k + c_g) mod p)
+ * mod G (the same family as the tables' hash functions, p = 4294967291, with
+ * constants of its own, so g is independent of every h_i) sends each key to
+ * one shard, and each shard is an ordinary table of the keys it received. A
+ * build partitions each rank's pairs by g, exchanges them (one all-to-all),
+ * and builds the shard; a find partitions the queries by g remembering their
+ * positions, exchanges them, finds them in the shard, exchanges the answers
+ * back and returns them to query order (ght_unpermute). The exchanges are
+ * the caller's collectives (torch.distributed in the Python binding).
+ * ------------------------------------------------------------------------- */
+#define GHT_PARTITION_SEED_SALT 0x5348415244ull /* a_g, c_g derive from seed XOR this */
+
+/* a_g and c_g of the partition hash for `seed`: the tables' derivation
+ * (SplitMix64, a = 1 + x mod (p-1), c = y mod p) from seed XOR
+ * GHT_PARTITION_SEED_SALT, attempt 0. Host only. */
+int ght_partition_constants(uint64_t seed, uint32_t *a, uint32_t *c);
+
+/* Reorder n keys by shard g(k) (shards in [1, 4096]) into d_out_keys, shard
+ * 0's keys first, with d_values carried alongside into d_out_values; if
+ * d_values is NULL, d_out_values receives each key's input position (for
+ * ght_unpermute). h_counts[s] receives the number of keys of shard s. The
+ * key 0xFFFFFFFF goes to shard 0. Order within a shard is unspecified.
+ * d_keys and d_values must be 16-byte aligned; n < 2^32. Runs on cuda_stream
+ * (NULL = legacy default) with scratch from the library's pool and waits for
+ * the counts. */
+int ght_partition(const uint32_t *d_keys, const uint32_t *d_values, uint64_t n, uint64_t seed, uint32_t shards,
+                  uint32_t *d_out_keys, uint32_t *d_out_values, uint64_t *h_counts, void *cuda_stream);
+
+/* d_dst[d_pos[j]] = d_src[j] for j < n (d_pos a permutation of [0, n));
+ * asynchronous on cuda_stream. */
+int ght_unpermute(const uint32_t *d_src, const uint32_t *d_pos, uint64_t n, uint32_t *d_dst, void *cuda_stream);
+
 /* Device scratch a build of n keys uses for grouping (0 if this table
  * builds without grouping). */
 uint64_t ght_build_scratch_bytes(const ght_table *t, uint64_t n);

@@ -149,6 +149,9 @@ def lib():
                 "ght_hash_device": ([vp, vp, vp, u64], i32),
                 "ght_hash_host": ([u32, u32, u32, vp, vp, u64], i32),
                 "ght_probe_lines": ([i32, vp, u64, u64, u32, vp], i32),
+                "ght_partition_constants": ([u64, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)], i32),
+                "ght_partition": ([vp, vp, u64, u64, u32, vp, vp, vp, vp], i32),
+                "ght_unpermute": ([vp, vp, u64, vp, vp], i32),
                 "ght_destroy": ([vp], None),
                 "ght_batch_create": ([C.c_uint32, vp, vp, u64, C.POINTER(GhtConfig)], vp),
                 "ght_batch_set_stream": ([vp, vp], i32),
@@ -304,6 +307,22 @@ def ght_hash_host(a: int, c: int, m: int, h_keys, h_out, n: int) -> None:
 def ght_probe_lines(mode: int, d_lines, num_lines: int, ops: int, seed: int = 1, stream: int = 0) -> None:
     """Memory-system ceiling probe on random 128-byte lines (asynchronous on `stream`)."""
     _check(lib().ght_probe_lines(mode, _ptr(d_lines), num_lines, ops, seed, stream))
+
+
+def ght_partition_constants(seed: int) -> tuple[int, int]:
+    a, c = C.c_uint32(0), C.c_uint32(0)
+    _check(lib().ght_partition_constants(seed, C.byref(a), C.byref(c)))
+    return a.value, c.value
+
+
+def ght_partition(d_keys, d_values, n: int, seed: int, shards: int, d_out_keys, d_out_values, h_counts,
+                  stream: int = 0) -> None:
+    _check(lib().ght_partition(_ptr(d_keys), _ptr(d_values), n, seed, shards, _ptr(d_out_keys),
+                               _ptr(d_out_values), _ptr(h_counts), stream))
+
+
+def ght_unpermute(d_src, d_pos, n: int, d_dst, stream: int = 0) -> None:
+    _check(lib().ght_unpermute(_ptr(d_src), _ptr(d_pos), n, _ptr(d_dst), stream))
 
 
 def ght_destroy(t: int) -> None:

@@ -154,9 +154,13 @@ cudaError_t launch_hash(const TableView &tv, const uint32_t *k, uint32_t *out, u
 cudaError_t launch_line_probe(int mode, void *lines, uint64_t num_lines, uint64_t ops, uint32_t seed,
                               cudaStream_t s);
 
-// kern_group.cu: reorder (keys, values) by H_0(k) >> shift into out_k/out_v.
+// kern_group.cu: reorder (keys, values) by H_0(k) >> shift into out_k/out_v
+// (values NULL: out_v receives each item's input position); counts[g] = items
+// of group g, cursors[g] = end of group g in the output.
 cudaError_t launch_group(const TableView &tv, const uint32_t *keys, const uint32_t *values, uint64_t n,
                          int shift, uint32_t groups, uint32_t *counts, uint32_t *cursors, uint32_t *out_k,
                          uint32_t *out_v, cudaStream_t s);
+// dst[pos[j]] = src[j] for j < n.
+cudaError_t launch_unpermute(const uint32_t *src, const uint32_t *pos, uint64_t n, uint32_t *dst, cudaStream_t s);
 
 }  // namespace ght

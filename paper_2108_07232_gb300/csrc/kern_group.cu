@@ -110,6 +110,8 @@ size_t group_scatter_smem(uint32_t groups) {
   return 4ull * kGroupTile * sizeof(uint32_t) + kGroupTile * sizeof(uint16_t) + 3ull * groups * sizeof(uint32_t);
 }
 
+// POS: the values are the items' input positions (values is not read).
+template <bool POS>
 __global__ void __launch_bounds__(kGroupThreads, 3)
 group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint32_t *__restrict__ values,
                      uint64_t n, int shift, uint32_t groups, uint32_t *__restrict__ cursors,
@@ -139,10 +141,10 @@ group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint
     const uint32_t bytes = (tn / 4u) * 16u;
     uint32_t *dk = bufs + 2 * b * kGroupTile;
     fence_proxy_async_smem();
-    mbar_arrive_expect_tx(&bars[b], 2u * bytes);
+    mbar_arrive_expect_tx(&bars[b], (POS ? 1u : 2u) * bytes);
     if (bytes) {
       bulk_g2s(dk, keys + t0, bytes, &bars[b]);
-      bulk_g2s(dk + kGroupTile, values + t0, bytes, &bars[b]);
+      if (!POS) bulk_g2s(dk + kGroupTile, values + t0, bytes, &bars[b]);
     }
   };
   uint32_t j = 0;  // this block's tile count so far
@@ -172,7 +174,7 @@ group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint
       const uint32_t i = (uint32_t)u * kGroupThreads + tid;
       if (i < tn) {
         k[u] = i < tbulk ? sk[i] : __ldg(keys + t0 + i);
-        v[u] = i < tbulk ? sv[i] : __ldg(values + t0 + i);
+        v[u] = POS ? (uint32_t)(t0 + i) : (i < tbulk ? sv[i] : __ldg(values + t0 + i));
         const uint32_t g = group_of(tv, k[u], shift);
         gr[u] = (g << 16) | atomicAdd(&cnt[g], 1u);  // group < 4096, rank < kGroupTile
       }
@@ -239,11 +241,30 @@ group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint
   }
 }
 
+// dst[pos[j]] = src[j]: answers of position-carrying items back to input order.
+__global__ void __launch_bounds__(256)
+unpermute_kernel(const uint32_t *__restrict__ src, const uint32_t *__restrict__ pos, uint64_t n,
+                 uint32_t *__restrict__ dst) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride)
+    dst[__ldg(pos + j)] = __ldg(src + j);
+}
+
+cudaError_t launch_unpermute(const uint32_t *src, const uint32_t *pos, uint64_t n, uint32_t *dst, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  int blocks = 0;
+  const cudaError_t e = grid_for(unpermute_kernel, n, 0, &blocks);
+  if (e != cudaSuccess) return e;
+  unpermute_kernel<<<blocks, 256, 0, s>>>(src, pos, n, dst);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_group(const TableView &tv, const uint32_t *keys, const uint32_t *values, uint64_t n,
                          int shift, uint32_t groups, uint32_t *counts, uint32_t *cursors, uint32_t *out_k,
                          uint32_t *out_v, cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
+  if (n == 0) return cudaMemsetAsync(counts, 0, groups * sizeof(uint32_t), s);
   if (n > 0xFFFFFFFFull || groups == 0 || groups > kMaxGroups) return cudaErrorInvalidValue;
+  const bool pos = values == nullptr;  // carry input positions instead of values
   if ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(values)) & 15u) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(counts, 0, groups * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
@@ -256,9 +277,10 @@ cudaError_t launch_group(const TableView &tv, const uint32_t *keys, const uint32
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const uint64_t tiles = (n + kGroupTile - 1) / kGroupTile;
   const size_t smem = group_scatter_smem(groups);
-  e = grid_for_smem(group_scatter_kernel, kGroupThreads, smem, tiles * kGroupThreads, 0, &blocks);
+  auto kern = pos ? group_scatter_kernel<true> : group_scatter_kernel<false>;
+  e = grid_for_smem(kern, kGroupThreads, smem, tiles * kGroupThreads, 0, &blocks);
   if (e != cudaSuccess) return e;
-  group_scatter_kernel<<<blocks, kGroupThreads, smem, s>>>(tv, keys, values, n, shift, groups, cursors, out_k, out_v);
+  kern<<<blocks, kGroupThreads, smem, s>>>(tv, keys, values, n, shift, groups, cursors, out_k, out_v);
   return cudaGetLastError();
 }
 
