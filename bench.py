@@ -380,6 +380,54 @@ def run_ours(args, world, rank, local):
     value = whole_job_value(keys_per_step, args.steps, world, ms)
     gpu_launches = launches[0]
 
+    # end to end through the public API from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hk, hv = keys.cpu().pin_memory(), vals.cpu().pin_memory()
+        hp, hn = pos.cpu().pin_memory(), neg.cpu().pin_memory()
+        hout = torch.empty_like(hk).pin_memory()
+
+        call_ms = {f"{op}@{lf}": [] for lf in LFS for op in ("build", "find_pos", "find_neg")}
+        h2d_gbs = {k: [] for k in call_ms}
+
+        def host_step():
+            # each call returns once its results are on the host, so the wall
+            # time of each is its end-to-end time
+            for lf in LFS:
+                t = tables[lf]
+                for op, fn in (("build", lambda: t.build(hk, hv)), ("find_pos", lambda: t.find(hp, hout)),
+                               ("find_neg", lambda: t.find(hn, hout))):
+                    c0 = time.perf_counter()
+                    fn()
+                    call_ms[f"{op}@{lf}"].append(1e3 * (time.perf_counter() - c0))
+                    s = t.stats()  # host-to-device copy span of that call (device events)
+                    if s["last_h2d_ms"] > 0:
+                        h2d_gbs[f"{op}@{lf}"].append(s["last_h2d_bytes"] / (s["last_h2d_ms"] / 1e3) / 1e9)
+            return int(hout[0])  # the step's result is on the host
+
+        for _ in range(max(1, args.warmup)):
+            host_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        step_ms = []
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            s0 = time.perf_counter()
+            host_step()
+            step_ms.append(round(1e3 * (time.perf_counter() - s0), 2))
+        torch.cuda.synchronize()
+        el = reduce_max(time.perf_counter() - t0, world, dev)
+        e2e = {"value": whole_job_value(keys_per_step, args.steps, world, 1e3 * el), "unit": "Gkeys/s",
+               "h2d_bytes_per_step": len(LFS) * (8 * n + 8 * n),
+               "d2h_bytes_per_step": len(LFS) * 8 * n,
+               "api": "HashTable.build/find on pinned CPU tensors (ght_build_host / ght_find_host)",
+               "step_ms": step_ms,
+               "call_ms": {k: round(statistics.median(v), 3) for k, v in call_ms.items()},
+               "call_ms_max": {k: round(max(v), 3) for k, v in call_ms.items()},
+               "h2d_gbs_median_min": {k: [round(statistics.median(v), 1), round(min(v), 1)]
+                                      for k, v in h2d_gbs.items() if v}}
+
     # probe counts for the algorithmic bytes: one extra counted build/find (untimed)
     probes = {}
     for lf in LFS:
@@ -449,49 +497,6 @@ def run_ours(args, world, rank, local):
         find_lines = (sum((probes[lf]["find_pos"] + probes[lf]["find_neg"]) * n for lf in LFS)
                       / sum((kernels[f"find_pos@{lf}"]["ms"] + kernels[f"find_neg@{lf}"]["ms"]) / 1e3 for lf in LFS))
         ceilings["kernels_glines_s"] = {"find": round(find_lines / 1e9, 2), "insert": round(ins_lines / 1e9, 2)}
-
-    # end to end through the public API from pinned host buffers
-    e2e = None
-    if not args.no_e2e:
-        hk, hv = keys.cpu().pin_memory(), vals.cpu().pin_memory()
-        hp, hn = pos.cpu().pin_memory(), neg.cpu().pin_memory()
-        hout = torch.empty_like(hk).pin_memory()
-
-        call_ms = {f"{op}@{lf}": [] for lf in LFS for op in ("build", "find_pos", "find_neg")}
-        h2d_gbs = {k: [] for k in call_ms}
-
-        def host_step():
-            # each call returns once its results are on the host, so the wall
-            # time of each is its end-to-end time
-            for lf in LFS:
-                t = tables[lf]
-                for op, fn in (("build", lambda: t.build(hk, hv)), ("find_pos", lambda: t.find(hp, hout)),
-                               ("find_neg", lambda: t.find(hn, hout))):
-                    c0 = time.perf_counter()
-                    fn()
-                    call_ms[f"{op}@{lf}"].append(1e3 * (time.perf_counter() - c0))
-                    s = t.stats()  # host-to-device copy span of that call (device events)
-                    if s["last_h2d_ms"] > 0:
-                        h2d_gbs[f"{op}@{lf}"].append(s["last_h2d_bytes"] / (s["last_h2d_ms"] / 1e3) / 1e9)
-            return int(hout[0])  # the step's result is on the host
-
-        host_step()
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            host_step()
-        torch.cuda.synchronize()
-        el = reduce_max(time.perf_counter() - t0, world, dev)
-        e2e = {"value": whole_job_value(keys_per_step, args.steps, world, 1e3 * el), "unit": "Gkeys/s",
-               "h2d_bytes_per_step": len(LFS) * (8 * n + 8 * n),
-               "d2h_bytes_per_step": len(LFS) * 8 * n,
-               "api": "HashTable.build/find on pinned CPU tensors (ght_build_host / ght_find_host)",
-               "call_ms": {k: round(statistics.median(v), 3) for k, v in call_ms.items()},
-               "call_ms_max": {k: round(max(v), 3) for k, v in call_ms.items()},
-               "h2d_gbs_median_min": {k: [round(statistics.median(v), 1), round(min(v), 1)]
-                                      for k, v in h2d_gbs.items() if v}}
 
     # the metric's served-latency clause and the batched path, measured on a
     # smaller scale beside the headline (rank 0 of a one-GPU run)
