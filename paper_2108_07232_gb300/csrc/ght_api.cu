@@ -578,7 +578,8 @@ int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n,
   return rc;
 }
 
-constexpr uint64_t kChunk = 1ull << 23;  // keys per host<->device pipeline chunk
+constexpr uint64_t kChunk = 1ull << 23;       // queries per host<->device pipeline chunk of a find
+constexpr uint64_t kBuildChunk = 1ull << 25;  // pairs per chunk of a host-buffer build (fewer insert launch tails)
 
 // check_duplicates: after a successful build from device keys, no key may be
 // stored twice; a duplicate leaves the table unbuilt.
@@ -787,8 +788,8 @@ int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_value
       cudaEventRecord(t->tev[1], t->stream);
       if (!ranked) cudaEventRecord(t->tev[2], t->stream);
       cudaEventRecord(t->tev[7], copy);
-      for (uint64_t off = 0, i = 0; rc == GHT_OK && off < n; off += kChunk, ++i) {
-        const uint64_t len = std::min(kChunk, n - off);
+      for (uint64_t off = 0, i = 0; rc == GHT_OK && off < n; off += kBuildChunk, ++i) {
+        const uint64_t len = std::min(kBuildChunk, n - off);
         cudaEvent_t ev = landed[i & 1];
         if ((e = cudaMemcpyAsync(d_k + off, h_keys + off, len * 4, cudaMemcpyHostToDevice, copy)) != cudaSuccess ||
             (e = cudaMemcpyAsync(d_v + off, h_values + off, len * 4, cudaMemcpyHostToDevice, copy)) != cudaSuccess ||

@@ -97,7 +97,7 @@ def test_two_phase_keys_only_set(G, lf, group):
 
 
 def test_two_phase_from_host_buffers(G):
-    n = (1 << 23) + (1 << 20) + 3  # two host-to-device chunks, the second ragged
+    n = (1 << 25) + (1 << 18) + 3  # two host-to-device chunks, the second ragged
     keys, vals = W.make_keys(n, 93), W.make_values(n, 93)
     t = G.HashTable("bcht", n, 0.97, seed=5, count_probes=1, ranked_build=1)
     t.build(keys, vals)  # CPU tensors: ght_build_host, placement overlapped with the copies
