@@ -99,8 +99,13 @@ group_scan_kernel(const uint32_t *__restrict__ counts, uint32_t groups, uint32_t
 // one contiguous run instead of scattered 4-byte stores. Keys and values
 // must be 16-byte aligned (the host checks); a tile's last n mod 4 items are
 // read directly.
-constexpr int kGroupThreads = 256;
-constexpr int kGroupPerThread = 15;  // 3840-pair tiles: 70 KB of shared memory, three blocks per SM
+constexpr int kGroupThreads = 384;
+// 6144-pair tiles: 111 KB of shared memory, two blocks (24 warps) per SM.
+// The tile's fixed cost (a prefix over every group, one reservation per
+// group) is what large tiles amortise: at 2^28 pairs the grouping took 2.98
+// / 2.25 / 1.73 / 1.67 ms with 2560 / 3840 / 6144 (512 threads) / 6144 (384
+// threads) pairs per tile.
+constexpr int kGroupPerThread = 16;
 constexpr int kGroupTile = kGroupThreads * kGroupPerThread;
 constexpr uint32_t kGroupWaitPolls = 1u << 26;  // bounded wait for a tile's copies
 
@@ -112,7 +117,7 @@ size_t group_scatter_smem(uint32_t groups) {
 
 // POS: the values are the items' input positions (values is not read).
 template <bool POS>
-__global__ void __launch_bounds__(kGroupThreads, 3)
+__global__ void __launch_bounds__(kGroupThreads, 2)
 group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint32_t *__restrict__ values,
                      uint64_t n, int shift, uint32_t groups, uint32_t *__restrict__ cursors,
                      uint32_t *__restrict__ out_k, uint32_t *__restrict__ out_v) {
