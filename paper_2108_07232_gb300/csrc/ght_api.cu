@@ -206,10 +206,25 @@ void group_shape(uint64_t m, int *shift, uint32_t *groups) {
   *groups = (uint32_t)(((m - 1) >> *shift) + 1);
 }
 
-// Scratch of a grouped build: counts and cursors, then the regrouped keys and values.
-uint64_t group_scratch_bytes(uint64_t n) {
+// Region of each group in a two-phase grouped build: the grouping writes
+// group g's pairs from g * region on, which needs no count pass; the region
+// holds the mean group size plus eight standard deviations of a uniform
+// hash's group sizes and 64, so only inputs whose first-choice buckets
+// crowd far beyond a random hash's overflow it (the build then regroups with
+// exact offsets). 0: exact offsets (a region layout would not fit 32-bit
+// indices).
+uint32_t group_region(uint64_t n, uint32_t groups) {
+  if (n == 0 || groups == 0) return 0;
+  const double mean = (double)n / groups;
+  const uint64_t region = (uint64_t)std::ceil(mean + 8.0 * std::sqrt(mean) + 64.0);
+  return region * groups <= 0xFFFFFFFFull ? (uint32_t)region : 0u;
+}
+
+// Scratch of a grouped build: counts and cursors, then the regrouped keys and
+// values (`len` entries each).
+uint64_t group_scratch_bytes(uint64_t len) {
   const uint64_t head = 2ull * ght::kMaxGroups * sizeof(uint32_t);
-  const uint64_t arr = (n * sizeof(uint32_t) + 255ull) & ~255ull;
+  const uint64_t arr = (len * sizeof(uint32_t) + 255ull) & ~255ull;
   return head + 2 * arr;
 }
 
@@ -423,8 +438,19 @@ bool wants_ranked(const ght_table *t, uint64_t n) {
   return t->shape.ranked_build > 0 || wants_grouping(t, n);
 }
 
+// Entries of the regrouped arrays of a build of n pairs (the groups' regions
+// when the build places by rank, else n).
+uint64_t grouped_len(const ght_table *t, uint64_t n) {
+  int shift = 0;
+  uint32_t groups = 1;
+  group_shape(t->shape.m, &shift, &groups);
+  const uint32_t region = wants_ranked(t, n) ? group_region(n, groups) : 0u;
+  return region ? (uint64_t)groups * region : n;
+}
+
 uint64_t build_scratch_need(const ght_table *t, uint64_t n) {
-  return (wants_grouping(t, n) ? group_scratch_bytes(n) : 0) + (wants_ranked(t, n) ? place_scratch_bytes(t->shape.m, n) : 0);
+  return (wants_grouping(t, n) ? group_scratch_bytes(grouped_len(t, n)) : 0) +
+         (wants_ranked(t, n) ? place_scratch_bytes(t->shape.m, n) : 0);
 }
 
 // Scratch of a two- or grouped-phase build: the caller's, else (for tables on
@@ -490,13 +516,16 @@ int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n,
   int shift = 0;
   uint32_t groups = 1;
   group_shape(t->shape.m, &shift, &groups);
+  // grouped pairs in per-group regions when placed by rank (no count pass)
+  const uint64_t glen = grouped ? grouped_len(t, n) : n;
+  uint32_t region = grouped && ranked && glen != n ? group_region(n, groups) : 0u;
   uint32_t *counts = reinterpret_cast<uint32_t *>(scr);
   uint32_t *cursors = counts + ght::kMaxGroups;
   uint32_t *gk = reinterpret_cast<uint32_t *>(scr + 2ull * ght::kMaxGroups * sizeof(uint32_t));
-  uint32_t *gv = gk + (((n * sizeof(uint32_t) + 255ull) & ~255ull) / sizeof(uint32_t));
+  uint32_t *gv = gk + align256(glen * sizeof(uint32_t)) / sizeof(uint32_t);
   // scratch layout: [grouping: counts, cursors, keys, values][ranked placement]
   const ght::PlaceBuffers pb =
-      ranked ? place_buffers(scr + (grouped ? group_scratch_bytes(n) : 0), t->shape.m, n) : ght::PlaceBuffers();
+      ranked ? place_buffers(scr + (grouped ? group_scratch_bytes(glen) : 0), t->shape.m, n) : ght::PlaceBuffers();
   int rc = fail(GHT_ERR_BUILD_FAILED, "build failed in %u attempts (chain bound or full buckets)",
                 t->shape.max_attempts);
   for (uint32_t attempt = first_attempt; attempt < t->shape.max_attempts; ++attempt) {
@@ -511,7 +540,7 @@ int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n,
     bool this_ranked = false;
     t->place_overflow = 0;
     if (grouped) {
-      e = ght::launch_group(tv, k, v ? v : k, n, shift, groups, counts, cursors, gk, gv, t->stream);
+      e = ght::launch_group(tv, k, v ? v : k, n, shift, groups, counts, cursors, gk, gv, t->stream, region);
       if (e != cudaSuccess) { rc = cuda_fail(e, "launching grouping"); break; }
       ik = gk;
       iv = gv;
@@ -521,13 +550,26 @@ int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n,
       // phase 1: ranked first-choice placement (of the grouped pairs, when
       // grouped: the stores then stay in a few MB of the table, whose lines
       // fill up in L2); its overflow goes to phase 2
+      ght::PlaceBuffers pa = pb;
+      if (region) {  // the pairs of group g are [g * region, cursors[g])
+        pa.ends = cursors;
+        pa.region = region;
+        pa.region_M = ght::make_fastmod(region).M;
+      }
       if ((e = cudaMemsetAsync(pb.counters, 0, t->shape.m * sizeof(uint32_t), t->stream)) != cudaSuccess ||
-          (e = launch_place(t, ik, iv, n, pb)) != cudaSuccess) {
+          (e = launch_place(t, ik, iv, region ? (uint64_t)groups * region : n, pa)) != cudaSuccess) {
         rc = cuda_fail(e, "launching the ranked placement");
         break;
       }
       cudaEventRecord(t->tev[2], t->stream);
       if ((rc = read_ctrl(t)) != GHT_OK) break;
+      if (region && ((t->h_ctrl->status & ght::kStatusGroupRegion) || t->h_ctrl->reserved[0] > pb.cap)) {
+        // a group outgrew its region, or the overflow outgrew its list: this
+        // attempt again with exact group offsets (its fallback reads dense arrays)
+        region = 0;
+        --attempt;
+        continue;
+      }
       if (t->h_ctrl->status & ght::kStatusSentinel) { rc = fail(GHT_ERR_SENTINEL_KEY, "an input key is the sentinel 0xFFFFFFFF"); break; }
       const uint64_t ovf = t->h_ctrl->reserved[0];
       t->place_overflow = ovf;

@@ -114,7 +114,16 @@ struct PlaceBuffers {
   uint32_t *ovf_k = nullptr;
   uint32_t *ovf_v = nullptr;
   uint64_t cap = 0;
+  // Grouped input in regions of `region` items per group (0: a dense input):
+  // group g's pairs are [g * region, ends[g]); the rest of its region is unused.
+  const uint32_t *ends = nullptr;
+  uint32_t region = 0;
+  uint64_t region_M = 0;  // Lemire-Kaser-Kurz constant of `region`: i / region = mulhi(region_M, i)
 };
+
+// Status bit of a grouping into fixed regions: some group had more pairs than
+// its region holds (the pairs beyond it were not written).
+constexpr uint32_t kStatusGroupRegion = 32u;
 
 // kern_bcht.cu
 cudaError_t launch_place_bcht(int B, const TableView &tv, const uint32_t *k, const uint32_t *v, uint64_t n,
@@ -157,9 +166,12 @@ cudaError_t launch_line_probe(int mode, void *lines, uint64_t num_lines, uint64_
 // kern_group.cu: reorder (keys, values) by H_0(k) >> shift into out_k/out_v
 // (values NULL: out_v receives each item's input position); counts[g] = items
 // of group g, cursors[g] = end of group g in the output.
+// region > 0: no count pass; group g's pairs go to [g * region, ...) and
+// cursors[g] ends as the end of its pairs (counts is not written); a group
+// with more than `region` pairs sets kStatusGroupRegion in tv.ctrl.
 cudaError_t launch_group(const TableView &tv, const uint32_t *keys, const uint32_t *values, uint64_t n,
                          int shift, uint32_t groups, uint32_t *counts, uint32_t *cursors, uint32_t *out_k,
-                         uint32_t *out_v, cudaStream_t s);
+                         uint32_t *out_v, cudaStream_t s, uint32_t region = 0);
 // dst[pos[j]] = src[j] for j < n.
 cudaError_t launch_unpermute(const uint32_t *src, const uint32_t *pos, uint64_t n, uint32_t *dst, cudaStream_t s);
 

@@ -415,7 +415,8 @@ bucketed_insert_kernel(TableView tv, const uint32_t *__restrict__ keys,
 // and appended to the list one block tile at a time with a single global
 // reservation on the control block's overflow count; entries past `cap` are
 // not written (the caller sees the count exceed cap and builds the ordinary
-// way).
+// way). With region > 0 the input is grouped into regions of `region` items
+// and only [g * region, ends[g]) of group g's region holds pairs.
 constexpr int kPlacePerThread = 4;
 constexpr int kPlaceTile = 256 * kPlacePerThread;
 
@@ -423,7 +424,8 @@ template <int B, bool COUNT, typename S = PairSlot>
 __global__ void __launch_bounds__(256)
 rank_place_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint32_t *__restrict__ values,
                   uint64_t n, uint32_t *__restrict__ counters, uint32_t *__restrict__ ovf_k,
-                  uint32_t *__restrict__ ovf_v, uint64_t cap) {
+                  uint32_t *__restrict__ ovf_v, uint64_t cap, const uint32_t *__restrict__ ends, uint32_t region,
+                  uint64_t region_M) {
   using T = typename S::T;
   T *slots = reinterpret_cast<T *>(tv.slots);
   unsigned long long *ovf_count = &tv.ctrl->reserved[0];
@@ -453,6 +455,7 @@ rank_place_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint32_
     for (int u = 0; u < kPlacePerThread; ++u) {
       const uint64_t i = t0 + (uint64_t)u * blockDim.x + threadIdx.x;  // coalesced
       ok[u] = i < n;
+      if (region && ok[u]) ok[u] = (uint32_t)i < __ldg(ends + __umul64hi(region_M, i));  // within its group's pairs
       k[u] = ok[u] ? __ldg(keys + i) : kEmptyKey;
       v[u] = ok[u] ? __ldg(values + i) : 0u;
       if (ok[u] && k[u] == kEmptyKey) {

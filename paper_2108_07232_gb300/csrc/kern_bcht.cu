@@ -47,7 +47,8 @@ static cudaError_t place_b(const TableView &tv, const uint32_t *k, const uint32_
   int blocks = 0;
   cudaError_t e = grid_for(kern, (n + kPlacePerThread - 1) / kPlacePerThread, 0, &blocks);
   if (e != cudaSuccess) return e;
-  kern<<<blocks, kThreads, 0, s>>>(tv, k, v, n, pb.counters, pb.ovf_k, pb.ovf_v, pb.cap);
+  kern<<<blocks, kThreads, 0, s>>>(tv, k, v, n, pb.counters, pb.ovf_k, pb.ovf_v, pb.cap, pb.ends, pb.region,
+                                       pb.region_M);
   return cudaGetLastError();
 }
 

@@ -120,7 +120,7 @@ template <bool POS>
 __global__ void __launch_bounds__(kGroupThreads, 2)
 group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint32_t *__restrict__ values,
                      uint64_t n, int shift, uint32_t groups, uint32_t *__restrict__ cursors,
-                     uint32_t *__restrict__ out_k, uint32_t *__restrict__ out_v) {
+                     uint32_t *__restrict__ out_k, uint32_t *__restrict__ out_v, uint32_t region) {
   extern __shared__ uint4 gs_smem[];
   uint32_t *bufs = reinterpret_cast<uint32_t *>(gs_smem);  // [2][keys kGroupTile | values kGroupTile]
   uint16_t *gid = reinterpret_cast<uint16_t *>(bufs + 4 * kGroupTile);  // [kGroupTile] group of each reordered item
@@ -239,11 +239,21 @@ group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint
     for (uint32_t i = tid; i < tn; i += kGroupThreads) {
       const uint32_t g = gid[i];
       const uint32_t at = base[g] + (i - pre[g]);
+      if (region && at >= (g + 1u) * region) {  // beyond the group's region: the caller regroups exactly
+        atomicOr(&tv.ctrl->status, kStatusGroupRegion);
+        continue;
+      }
       out_k[at] = sk[i];
       out_v[at] = sv[i];
     }
     __syncthreads();
   }
+}
+
+// Region mode: each group's cursor starts at the group's region.
+__global__ void region_cursors_kernel(uint32_t *__restrict__ cursors, uint32_t groups, uint32_t region) {
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += gridDim.x * blockDim.x)
+    cursors[g] = g * region;
 }
 
 // dst[pos[j]] = src[j]: answers of position-carrying items back to input order.
@@ -266,26 +276,36 @@ cudaError_t launch_unpermute(const uint32_t *src, const uint32_t *pos, uint64_t 
 
 cudaError_t launch_group(const TableView &tv, const uint32_t *keys, const uint32_t *values, uint64_t n,
                          int shift, uint32_t groups, uint32_t *counts, uint32_t *cursors, uint32_t *out_k,
-                         uint32_t *out_v, cudaStream_t s) {
-  if (n == 0) return cudaMemsetAsync(counts, 0, groups * sizeof(uint32_t), s);
-  if (n > 0xFFFFFFFFull || groups == 0 || groups > kMaxGroups) return cudaErrorInvalidValue;
+                         uint32_t *out_v, cudaStream_t s, uint32_t region) {
+  if (groups == 0 || groups > kMaxGroups) return cudaErrorInvalidValue;
+  if (region) {
+    if ((uint64_t)groups * region > 0xFFFFFFFFull) return cudaErrorInvalidValue;
+    region_cursors_kernel<<<(groups + 255) / 256, 256, 0, s>>>(cursors, groups, region);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || n == 0) return e;
+  } else if (n == 0) {
+    return cudaMemsetAsync(counts, 0, groups * sizeof(uint32_t), s);
+  }
+  if (n > 0xFFFFFFFFull) return cudaErrorInvalidValue;
   const bool pos = values == nullptr;  // carry input positions instead of values
   if ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(values)) & 15u) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemsetAsync(counts, 0, groups * sizeof(uint32_t), s);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
   int blocks = 0;
-  e = grid_for(group_count_kernel, n, 0, &blocks);
-  if (e != cudaSuccess) return e;
-  group_count_kernel<<<blocks, 256, groups * sizeof(uint32_t), s>>>(tv, keys, n, shift, groups, counts);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  group_scan_kernel<<<1, 1024, 0, s>>>(counts, groups, cursors);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (!region) {  // exact offsets: count pass and prefix
+    if ((e = cudaMemsetAsync(counts, 0, groups * sizeof(uint32_t), s)) != cudaSuccess) return e;
+    e = grid_for(group_count_kernel, n, 0, &blocks);
+    if (e != cudaSuccess) return e;
+    group_count_kernel<<<blocks, 256, groups * sizeof(uint32_t), s>>>(tv, keys, n, shift, groups, counts);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    group_scan_kernel<<<1, 1024, 0, s>>>(counts, groups, cursors);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   const uint64_t tiles = (n + kGroupTile - 1) / kGroupTile;
   const size_t smem = group_scatter_smem(groups);
   auto kern = pos ? group_scatter_kernel<true> : group_scatter_kernel<false>;
   e = grid_for_smem(kern, kGroupThreads, smem, tiles * kGroupThreads, 0, &blocks);
   if (e != cudaSuccess) return e;
-  kern<<<blocks, kGroupThreads, smem, s>>>(tv, keys, values, n, shift, groups, cursors, out_k, out_v);
+  kern<<<blocks, kGroupThreads, smem, s>>>(tv, keys, values, n, shift, groups, cursors, out_k, out_v, region);
   return cudaGetLastError();
 }
 

@@ -42,7 +42,8 @@ cudaError_t launch_place_set(const TableView &tv, const uint32_t *k, uint64_t n,
   cudaError_t e = grid_for(kern, (n + kPlacePerThread - 1) / kPlacePerThread, 0, &blocks);
   if (e != cudaSuccess) return e;
   // a set has no values: the key array stands in for them and is ignored
-  kern<<<blocks, kThreads, 0, s>>>(tv, k, k, n, pb.counters, pb.ovf_k, pb.ovf_v, pb.cap);
+  kern<<<blocks, kThreads, 0, s>>>(tv, k, k, n, pb.counters, pb.ovf_k, pb.ovf_v, pb.cap, pb.ends, pb.region,
+                                       pb.region_M);
   return cudaGetLastError();
 }
 
