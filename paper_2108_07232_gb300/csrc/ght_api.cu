@@ -438,6 +438,30 @@ bool wants_ranked(const ght_table *t, uint64_t n) {
   return t->shape.ranked_build > 0 || wants_grouping(t, n);
 }
 
+// Second-level split of a two-phase grouped build (the block placement):
+// sub-groups of 2^fine_shift buckets (64 KB of table each), 2^subs_log2 <=
+// 128 per group, `bins` in all, each in a region of region2 pairs. False
+// where the first level's regions are too small or the split too fine.
+struct SubShape {
+  int fine_shift = 0, subs_log2 = 0;
+  uint32_t bins = 0, region2 = 0;
+};
+
+bool sub_shape(const Shape &s, uint64_t n, int shift, uint32_t region1, SubShape *out) {
+  if (region1 < ght::kSubgroupMinRegion) return false;
+  const uint64_t m = s.m;
+  const int fine = ght::block_place_fine_shift(s.b, s.scheme == GHT_BCHT_SET);
+  SubShape sh;
+  sh.fine_shift = shift < fine ? shift : fine;
+  sh.subs_log2 = shift - sh.fine_shift;
+  if (sh.subs_log2 > 7) return false;
+  sh.bins = (uint32_t)(((m - 1) >> sh.fine_shift) + 1);
+  sh.region2 = group_region(n, sh.bins);
+  if (!sh.region2) return false;
+  *out = sh;
+  return true;
+}
+
 // Entries of the regrouped arrays of a build of n pairs (the groups' regions
 // when the build places by rank, else n).
 uint64_t grouped_len(const ght_table *t, uint64_t n) {
@@ -448,9 +472,21 @@ uint64_t grouped_len(const ght_table *t, uint64_t n) {
   return region ? (uint64_t)groups * region : n;
 }
 
+// Scratch of the second-level split: the split pairs and one cursor per
+// sub-group (0 where the build does not use it).
+uint64_t sub_scratch_bytes(const ght_table *t, uint64_t n) {
+  if (!wants_grouping(t, n) || !wants_ranked(t, n)) return 0;
+  int shift = 0;
+  uint32_t groups = 1;
+  group_shape(t->shape.m, &shift, &groups);
+  SubShape sh;
+  if (!sub_shape(t->shape, n, shift, group_region(n, groups), &sh)) return 0;
+  return 2 * align256((uint64_t)sh.bins * sh.region2 * sizeof(uint32_t)) + align256(sh.bins * sizeof(uint32_t));
+}
+
 uint64_t build_scratch_need(const ght_table *t, uint64_t n) {
   return (wants_grouping(t, n) ? group_scratch_bytes(grouped_len(t, n)) : 0) +
-         (wants_ranked(t, n) ? place_scratch_bytes(t->shape.m, n) : 0);
+         (wants_ranked(t, n) ? place_scratch_bytes(t->shape.m, n) : 0) + sub_scratch_bytes(t, n);
 }
 
 // Scratch of a two- or grouped-phase build: the caller's, else (for tables on
@@ -526,13 +562,25 @@ int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n,
   // scratch layout: [grouping: counts, cursors, keys, values][ranked placement]
   const ght::PlaceBuffers pb =
       ranked ? place_buffers(scr + (grouped ? group_scratch_bytes(glen) : 0), t->shape.m, n) : ght::PlaceBuffers();
+  // second-level split and block placement: [sub-group keys, values, cursors] after the placement scratch
+  SubShape sub;
+  bool two_level = region && sub_shape(t->shape, n, shift, region, &sub) && sub_scratch_bytes(t, n) > 0;
+  uint32_t *sk = nullptr, *sv = nullptr, *scur = nullptr;
+  if (two_level) {
+    char *p = scr + group_scratch_bytes(glen) + place_scratch_bytes(t->shape.m, n);
+    const uint64_t arr = align256((uint64_t)sub.bins * sub.region2 * sizeof(uint32_t));
+    sk = reinterpret_cast<uint32_t *>(p);
+    sv = reinterpret_cast<uint32_t *>(p + arr);
+    scur = reinterpret_cast<uint32_t *>(p + 2 * arr);
+  }
   int rc = fail(GHT_ERR_BUILD_FAILED, "build failed in %u attempts (chain bound or full buckets)",
                 t->shape.max_attempts);
   for (uint32_t attempt = first_attempt; attempt < t->shape.max_attempts; ++attempt) {
     t->derive(attempt);
     const ght::TableView tv = t->view();
     cudaEventRecord(t->tev[0], t->stream);
-    cudaError_t e = ght::launch_fill(tv, t->words(), t->stream);
+    // the block placement writes every table line: only the control block is reset
+    cudaError_t e = two_level ? cudaMemsetAsync(t->ctrl, 0, kCtrlBytes, t->stream) : ght::launch_fill(tv, t->words(), t->stream);
     if (e != cudaSuccess) { rc = cuda_fail(e, "launching fill"); break; }
     cudaEventRecord(t->tev[1], t->stream);
     const uint32_t *ik = k, *iv = v;  // what the cuckoo insert takes
@@ -541,6 +589,16 @@ int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n,
     t->place_overflow = 0;
     if (grouped) {
       e = ght::launch_group(tv, k, v ? v : k, n, shift, groups, counts, cursors, gk, gv, t->stream, region);
+      if (e == cudaSuccess && two_level) {
+        ght::SubSplit ss;
+        ss.ends1 = cursors;
+        ss.region1 = region;
+        ss.region1_M = ght::make_fastmod(region).M;
+        ss.fine_shift = sub.fine_shift;
+        ss.subs_log2 = sub.subs_log2;
+        e = ght::launch_subgroup(tv, gk, gv, (uint64_t)groups * region, ss, sub.bins, scur, sub.region2, sk, sv,
+                                 t->stream);
+      }
       if (e != cudaSuccess) { rc = cuda_fail(e, "launching grouping"); break; }
       ik = gk;
       iv = gv;
@@ -556,8 +614,13 @@ int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n,
         pa.region = region;
         pa.region_M = ght::make_fastmod(region).M;
       }
-      if ((e = cudaMemsetAsync(pb.counters, 0, t->shape.m * sizeof(uint32_t), t->stream)) != cudaSuccess ||
-          (e = launch_place(t, ik, iv, region ? (uint64_t)groups * region : n, pa)) != cudaSuccess) {
+      if (two_level) {
+        e = ght::launch_block_place(t->shape.b, t->shape.scheme == GHT_BCHT_SET, tv, sk, sv, scur, sub.region2,
+                                    sub.bins, sub.fine_shift, pb, t->shape.count_probes != 0, t->stream);
+      } else if ((e = cudaMemsetAsync(pb.counters, 0, t->shape.m * sizeof(uint32_t), t->stream)) == cudaSuccess) {
+        e = launch_place(t, ik, iv, region ? (uint64_t)groups * region : n, pa);
+      }
+      if (e != cudaSuccess) {
         rc = cuda_fail(e, "launching the ranked placement");
         break;
       }
@@ -565,8 +628,10 @@ int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n,
       if ((rc = read_ctrl(t)) != GHT_OK) break;
       if (region && ((t->h_ctrl->status & ght::kStatusGroupRegion) || t->h_ctrl->reserved[0] > pb.cap)) {
         // a group outgrew its region, or the overflow outgrew its list: this
-        // attempt again with exact group offsets (its fallback reads dense arrays)
+        // attempt again with exact group offsets and the filled table of the
+        // global-counter placement (its fallback reads dense arrays)
         region = 0;
+        two_level = false;
         --attempt;
         continue;
       }

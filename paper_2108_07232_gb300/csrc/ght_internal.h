@@ -166,6 +166,37 @@ cudaError_t launch_line_probe(int mode, void *lines, uint64_t num_lines, uint64_
 // kern_group.cu: reorder (keys, values) by H_0(k) >> shift into out_k/out_v
 // (values NULL: out_v receives each item's input position); counts[g] = items
 // of group g, cursors[g] = end of group g in the output.
+// Second-level split of a region-grouped array (launch_subgroup).
+struct SubSplit {
+  const uint32_t *ends1 = nullptr;  // per group: end of its pairs in the grouped array
+  uint32_t region1 = 0;             // the grouped array's region per group
+  uint64_t region1_M = 0;           // i / region1 = mulhi(region1_M, i)
+  int fine_shift = 0;               // sub-group of a key: H_0(k) >> fine_shift
+  int subs_log2 = 0;                // sub-groups per group, log2 (<= 7)
+};
+
+// Reorder the pairs of a region-grouped array (len entries, groups of
+// 2^subs_log2 <= 128 sub-groups) by sub-group into regions of `region` entries:
+// sub-group f's pairs go to [f * region, cursors[f]); bins = sub-groups in
+// all. A sub-group with more pairs than its region sets kStatusGroupRegion.
+cudaError_t launch_subgroup(const TableView &tv, const uint32_t *keys, const uint32_t *values, uint64_t len,
+                            const SubSplit &sub, uint32_t bins, uint32_t *cursors, uint32_t region, uint32_t *out_k,
+                            uint32_t *out_v, cudaStream_t s);
+
+// Smallest first-level region a second-level split accepts (a scatter tile
+// must span at most two groups).
+constexpr uint32_t kSubgroupMinRegion = 6144;
+
+// kern_place.cu: first-choice placement of sub-group-split pairs, one block
+// per sub-group of 2^fine_shift buckets (see block_place_kernel); writes every
+// table line, so the table needs no fill. Sub-group f's pairs are
+// [f * region, ends[f]) of pk/pv; bins sub-groups in all. fine_shift may not
+// exceed block_place_fine_shift (the sub-groups whose buckets fill 64 KB).
+int block_place_fine_shift(int B, bool key_slots);
+cudaError_t launch_block_place(int B, bool key_slots, const TableView &tv, const uint32_t *pk, const uint32_t *pv,
+                               const uint32_t *ends, uint32_t region, uint32_t bins, int fine_shift,
+                               const PlaceBuffers &pb, bool count, cudaStream_t s);
+
 // region > 0: no count pass; group g's pairs go to [g * region, ...) and
 // cursors[g] ends as the end of its pairs (counts is not written); a group
 // with more than `region` pairs sets kStatusGroupRegion in tv.ctrl.

@@ -116,11 +116,16 @@ size_t group_scatter_smem(uint32_t groups) {
 }
 
 // POS: the values are the items' input positions (values is not read).
-template <bool POS>
+// SUB: the input is itself grouped into regions (sub.ends1, sub.region1), and
+// each group is split further into 2^sub.subs_log2 sub-groups of
+// H_0 >> sub.fine_shift; a tile then spans at most two groups, so `groups`
+// (= 2 << subs_log2) local bins cover it, and bin j of a tile whose first
+// item lies in group g is sub-group (g << subs_log2) + j.
+template <bool POS, bool SUB>
 __global__ void __launch_bounds__(kGroupThreads, 2)
 group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint32_t *__restrict__ values,
                      uint64_t n, int shift, uint32_t groups, uint32_t *__restrict__ cursors,
-                     uint32_t *__restrict__ out_k, uint32_t *__restrict__ out_v, uint32_t region) {
+                     uint32_t *__restrict__ out_k, uint32_t *__restrict__ out_v, uint32_t region, SubSplit sub) {
   extern __shared__ uint4 gs_smem[];
   uint32_t *bufs = reinterpret_cast<uint32_t *>(gs_smem);  // [2][keys kGroupTile | values kGroupTile]
   uint16_t *gid = reinterpret_cast<uint16_t *>(bufs + 4 * kGroupTile);  // [kGroupTile] group of each reordered item
@@ -129,6 +134,7 @@ group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint
   uint32_t *base = pre + groups;                                          // [groups] reserved output position
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ uint32_t warp_sums[kGroupThreads / 32];
+  __shared__ uint32_t s_total;
   __shared__ int s_abort;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint64_t ntiles = (n + kGroupTile - 1) / kGroupTile;
@@ -173,15 +179,26 @@ group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint
     const uint32_t tn = (uint32_t)(n - t0 < (uint64_t)kGroupTile ? n - t0 : (uint64_t)kGroupTile);
     const uint32_t tbulk = tn & ~3u;  // items that came by the bulk copies
     uint32_t *sk = bufs + 2 * b * kGroupTile, *sv = sk + kGroupTile;
+    // SUB: the tile's first sub-group (of the group holding its first item)
+    const uint32_t bin0 = SUB ? (uint32_t)__umul64hi(sub.region1_M, t0) << sub.subs_log2 : 0u;
     uint32_t k[kGroupPerThread], v[kGroupPerThread], gr[kGroupPerThread];
 #pragma unroll
     for (int u = 0; u < kGroupPerThread; ++u) {
       const uint32_t i = (uint32_t)u * kGroupThreads + tid;
+      gr[u] = 0xFFFFFFFFu;  // no item
       if (i < tn) {
         k[u] = i < tbulk ? sk[i] : __ldg(keys + t0 + i);
         v[u] = POS ? (uint32_t)(t0 + i) : (i < tbulk ? sv[i] : __ldg(values + t0 + i));
-        const uint32_t g = group_of(tv, k[u], shift);
-        gr[u] = (g << 16) | atomicAdd(&cnt[g], 1u);  // group < 4096, rank < kGroupTile
+        bool valid = true;
+        uint32_t g;
+        if constexpr (SUB) {
+          // items past their group's pairs are the unused tail of its region
+          valid = (uint32_t)(t0 + i) < __ldg(sub.ends1 + __umul64hi(sub.region1_M, t0 + i));
+          g = (k[u] == kEmptyKey ? 0u : bucket_of(tv.hf, 0, k[u]) >> sub.fine_shift) - bin0;
+        } else {
+          g = group_of(tv, k[u], shift);
+        }
+        if (valid) gr[u] = (g << 16) | atomicAdd(&cnt[g], 1u);  // group < 4096, rank < kGroupTile
       }
     }
     __syncthreads();
@@ -202,28 +219,29 @@ group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint
     uint32_t before = 0;
     for (int w = 0; w < wid; ++w) before += warp_sums[w];
     uint32_t acc = before + incl - run;
+    if (tid == kGroupThreads - 1) s_total = acc + run;  // items of the tile (the valid ones)
+    uint32_t *cur = cursors + bin0;                      // this tile's cursors
     // reservations: with at most two groups per thread the atomics' results
     // stay in registers until after the reorder, so their round trip overlaps it
     uint32_t r0 = 0u, r1 = 0u;
     if (per <= 2) {
       const uint32_t c0 = g0 < g1 ? cnt[g0] : 0u, c1 = g0 + 1 < g1 ? cnt[g0 + 1] : 0u;
-      if (c0) r0 = atomicAdd(&cursors[g0], c0);
-      if (c1) r1 = atomicAdd(&cursors[g0 + 1], c1);
+      if (c0) r0 = atomicAdd(&cur[g0], c0);
+      if (c1) r1 = atomicAdd(&cur[g0 + 1], c1);
       if (g0 < g1) pre[g0] = acc;
       if (g0 + 1 < g1) pre[g0 + 1] = acc + c0;
     } else {
       for (uint32_t i = g0; i < g1; ++i) {
         pre[i] = acc;
         acc += cnt[i];
-        if (cnt[i]) base[i] = atomicAdd(&cursors[i], cnt[i]);
+        if (cnt[i]) base[i] = atomicAdd(&cur[i], cnt[i]);
       }
     }
     __syncthreads();
     // reorder by group in place (every item of the buffer was read above)
 #pragma unroll
     for (int u = 0; u < kGroupPerThread; ++u) {
-      const uint32_t i = (uint32_t)u * kGroupThreads + tid;
-      if (i < tn) {
+      if (gr[u] != 0xFFFFFFFFu) {
         const uint32_t g = gr[u] >> 16;
         const uint32_t at = pre[g] + (gr[u] & 0xFFFFu);
         sk[at] = k[u];
@@ -236,10 +254,11 @@ group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint
       if (g0 + 1 < g1) base[g0 + 1] = r1;
     }
     __syncthreads();
-    for (uint32_t i = tid; i < tn; i += kGroupThreads) {
+    const uint32_t tv_n = SUB ? s_total : tn;
+    for (uint32_t i = tid; i < tv_n; i += kGroupThreads) {
       const uint32_t g = gid[i];
       const uint32_t at = base[g] + (i - pre[g]);
-      if (region && at >= (g + 1u) * region) {  // beyond the group's region: the caller regroups exactly
+      if (region && at >= (bin0 + g + 1u) * region) {  // beyond the group's region: the caller regroups exactly
         atomicOr(&tv.ctrl->status, kStatusGroupRegion);
         continue;
       }
@@ -302,10 +321,33 @@ cudaError_t launch_group(const TableView &tv, const uint32_t *keys, const uint32
   }
   const uint64_t tiles = (n + kGroupTile - 1) / kGroupTile;
   const size_t smem = group_scatter_smem(groups);
-  auto kern = pos ? group_scatter_kernel<true> : group_scatter_kernel<false>;
+  auto kern = pos ? group_scatter_kernel<true, false> : group_scatter_kernel<false, false>;
   e = grid_for_smem(kern, kGroupThreads, smem, tiles * kGroupThreads, 0, &blocks);
   if (e != cudaSuccess) return e;
-  kern<<<blocks, kGroupThreads, smem, s>>>(tv, keys, values, n, shift, groups, cursors, out_k, out_v, region);
+  kern<<<blocks, kGroupThreads, smem, s>>>(tv, keys, values, n, shift, groups, cursors, out_k, out_v, region,
+                                           SubSplit());
+  return cudaGetLastError();
+}
+
+cudaError_t launch_subgroup(const TableView &tv, const uint32_t *keys, const uint32_t *values, uint64_t len,
+                            const SubSplit &sub, uint32_t bins, uint32_t *cursors, uint32_t region, uint32_t *out_k,
+                            uint32_t *out_v, cudaStream_t s) {
+  if (len > 0xFFFFFFFFull || (uint64_t)bins * region > 0xFFFFFFFFull || sub.subs_log2 > 7 || region == 0 ||
+      sub.region1 < kSubgroupMinRegion)
+    return cudaErrorInvalidValue;
+  static_assert(kGroupTile <= kSubgroupMinRegion, "a tile spans at most two groups");
+  if ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(values)) & 15u) return cudaErrorInvalidValue;
+  region_cursors_kernel<<<(bins + 255) / 256, 256, 0, s>>>(cursors, bins, region);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || len == 0) return e;
+  const uint32_t local = 2u << sub.subs_log2;  // a tile spans at most two groups
+  const uint64_t tiles = (len + kGroupTile - 1) / kGroupTile;
+  const size_t smem = group_scatter_smem(local);
+  int blocks = 0;
+  auto kern = group_scatter_kernel<false, true>;
+  e = grid_for_smem(kern, kGroupThreads, smem, tiles * kGroupThreads, 0, &blocks);
+  if (e != cudaSuccess) return e;
+  kern<<<blocks, kGroupThreads, smem, s>>>(tv, keys, values, len, 0, local, cursors, out_k, out_v, region, sub);
   return cudaGetLastError();
 }
 

@@ -196,3 +196,44 @@ def test_unaligned_arrays_build_ungrouped(G):
     assert (O._u32(t.find(q.cuda()).cpu()) == O.lookup(keys[1:], vals[1:], q)).all()
     t.build(dk[:n], dv[:n])  # aligned again: grouped
     assert t.stats()["last_build_grouped"] == 1
+
+
+@pytest.mark.parametrize("scheme,b,lf", [("bcht", 16, 0.99), ("bcht", 16, 0.9), ("bcht", 32, 0.99),
+                                         ("bcht_set", 32, 0.99)])
+def test_two_level_split_and_block_placement(G, scheme, b, lf):
+    """At 2^24 + 5 keys the grouped two-phase build splits each group again
+    into sub-groups of 2048 buckets and places each sub-group with one
+    thread block (shared-memory counters, every table line written by the
+    block, no fill): valid layout, bit-exact finds, probe counts that match
+    the oracle on the GPU's own table."""
+    n = (1 << 24) + 5
+    keys, vals = W.make_keys(n, 99), W.make_values(n, 99)
+    sets = scheme == "bcht_set"
+    zeros = torch.zeros(n, dtype=torch.int32)
+    t = G.HashTable(scheme, n, lf, seed=23, count_probes=1, group_build=1, bucket_size=b)
+    t.build(keys.cuda(), None if sets else vals.cuda())
+    st = t.stats()
+    assert st["built"] == 1 and st["last_build_ranked"] == 1 and st["last_build_grouped"] == 1
+    T = O.Table(O.BCHT, n, lf, b=b, m=st["num_buckets"])
+    T.set_constants(st["hash_a"], st["hash_c"])
+    raw = t.export()
+    if sets:
+        slots = np.where(raw == O.EMPTY, np.uint64(O.EMPTY_PAIR), raw.astype(np.uint64))
+        ok, msg = T.validate(keys, zeros, slots=slots)
+    else:
+        slots = raw
+        ok, msg = T.validate(keys, vals, slots=slots)
+    assert ok, msg
+    q = W.make_queries(keys, 1 << 20, 0.5, seed=8)
+    t.reset_counters()
+    got = O._u32(t.find(q.cuda()).cpu())
+    want = O.lookup(keys, zeros if sets else vals, q)
+    if sets:
+        want = (want != O.EMPTY).astype(np.uint32)
+    assert (got == want).all()
+    assert t.stats()["find_probes"] == T.find(q, slots=slots)[2]
+    S = O.Table(O.BCHT, n, lf, b=b, m=st["num_buckets"])
+    S.set_constants(st["hash_a"], st["hash_c"])
+    assert S.build(keys, zeros if sets else vals) == 1
+    gpu, cpu = st["insert_probes"] / n, S.stats.probes / n
+    assert abs(gpu - cpu) <= 0.05, (gpu, cpu)
