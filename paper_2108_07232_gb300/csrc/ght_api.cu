@@ -216,7 +216,7 @@ void group_shape(uint64_t m, int *shift, uint32_t *groups) {
 uint32_t group_region(uint64_t n, uint32_t groups) {
   if (n == 0 || groups == 0) return 0;
   const double mean = (double)n / groups;
-  const uint64_t region = (uint64_t)std::ceil(mean + 8.0 * std::sqrt(mean) + 64.0);
+  const uint64_t region = ((uint64_t)std::ceil(mean + 8.0 * std::sqrt(mean) + 64.0) + 7ull) & ~7ull;
   return region * groups <= 0xFFFFFFFFull ? (uint32_t)region : 0u;
 }
 
@@ -596,6 +596,7 @@ int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n,
         ss.region1_M = ght::make_fastmod(region).M;
         ss.fine_shift = sub.fine_shift;
         ss.subs_log2 = sub.subs_log2;
+        ss.groups = groups;
         e = ght::launch_subgroup(tv, gk, gv, (uint64_t)groups * region, ss, sub.bins, scur, sub.region2, sk, sv,
                                  t->stream);
       }

@@ -173,6 +173,7 @@ struct SubSplit {
   uint64_t region1_M = 0;           // i / region1 = mulhi(region1_M, i)
   int fine_shift = 0;               // sub-group of a key: H_0(k) >> fine_shift
   int subs_log2 = 0;                // sub-groups per group, log2 (<= 7)
+  uint32_t groups = 0;              // groups of the first level
 };
 
 // Reorder the pairs of a region-grouped array (len entries, groups of
@@ -183,8 +184,9 @@ cudaError_t launch_subgroup(const TableView &tv, const uint32_t *keys, const uin
                             const SubSplit &sub, uint32_t bins, uint32_t *cursors, uint32_t region, uint32_t *out_k,
                             uint32_t *out_v, cudaStream_t s);
 
-// Smallest first-level region a second-level split accepts (a scatter tile
-// must span at most two groups).
+// Smallest first-level region a second-level split accepts (smaller regions
+// would leave its tiles mostly empty). Regions are multiples of 8 entries, so
+// a region's tiles start on 16-byte boundaries.
 constexpr uint32_t kSubgroupMinRegion = 6144;
 
 // kern_place.cu: first-choice placement of sub-group-split pairs, one block

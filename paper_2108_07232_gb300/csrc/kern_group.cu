@@ -118,9 +118,10 @@ size_t group_scatter_smem(uint32_t groups) {
 // POS: the values are the items' input positions (values is not read).
 // SUB: the input is itself grouped into regions (sub.ends1, sub.region1), and
 // each group is split further into 2^sub.subs_log2 sub-groups of
-// H_0 >> sub.fine_shift; a tile then spans at most two groups, so `groups`
-// (= 2 << subs_log2) local bins cover it, and bin j of a tile whose first
-// item lies in group g is sub-group (g << subs_log2) + j.
+// H_0 >> sub.fine_shift. Tiles then follow the regions (tile t of group g
+// starts at g * region1 + t * kGroupTile and ends at most at ends1[g]), so
+// `groups` (= 1 << subs_log2) local bins cover a tile, and bin j of a tile of
+// group g is sub-group (g << subs_log2) + j.
 template <bool POS, bool SUB>
 __global__ void __launch_bounds__(kGroupThreads, 2)
 group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint32_t *__restrict__ values,
@@ -134,10 +135,22 @@ group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint
   uint32_t *base = pre + groups;                                          // [groups] reserved output position
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ uint32_t warp_sums[kGroupThreads / 32];
-  __shared__ uint32_t s_total;
   __shared__ int s_abort;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const uint64_t ntiles = (n + kGroupTile - 1) / kGroupTile;
+  // SUB: tiles per region; a tile's start and length follow its group's pairs
+  const uint32_t tpg = SUB ? (sub.region1 + kGroupTile - 1) / kGroupTile : 0u;
+  const uint64_t ntiles = SUB ? (uint64_t)sub.groups * tpg : (n + kGroupTile - 1) / kGroupTile;
+  auto tile_span = [&](uint64_t tile, uint64_t *t0, uint32_t *tn) {
+    if (SUB) {
+      const uint32_t g = (uint32_t)(tile / tpg), t = (uint32_t)(tile % tpg);
+      const uint64_t start = (uint64_t)g * sub.region1 + (uint64_t)t * kGroupTile, end = __ldg(sub.ends1 + g);
+      *t0 = start;
+      *tn = end > start ? (uint32_t)(end - start < (uint64_t)kGroupTile ? end - start : (uint64_t)kGroupTile) : 0u;
+    } else {
+      *t0 = tile * kGroupTile;
+      *tn = (uint32_t)(n - *t0 < (uint64_t)kGroupTile ? n - *t0 : (uint64_t)kGroupTile);
+    }
+  };
   if (tid == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
@@ -147,8 +160,9 @@ group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint
   __syncthreads();
   // thread 0: copy the whole 16-byte pieces of tile `tile` into buffer b
   auto issue = [&](uint64_t tile, int b) {
-    const uint64_t t0 = tile * kGroupTile;
-    const uint32_t tn = (uint32_t)(n - t0 < (uint64_t)kGroupTile ? n - t0 : (uint64_t)kGroupTile);
+    uint64_t t0;
+    uint32_t tn;
+    tile_span(tile, &t0, &tn);
     const uint32_t bytes = (tn / 4u) * 16u;
     uint32_t *dk = bufs + 2 * b * kGroupTile;
     fence_proxy_async_smem();
@@ -175,30 +189,23 @@ group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint
       }
       return;
     }
-    const uint64_t t0 = tile * kGroupTile;
-    const uint32_t tn = (uint32_t)(n - t0 < (uint64_t)kGroupTile ? n - t0 : (uint64_t)kGroupTile);
+    uint64_t t0;
+    uint32_t tn;
+    tile_span(tile, &t0, &tn);
     const uint32_t tbulk = tn & ~3u;  // items that came by the bulk copies
     uint32_t *sk = bufs + 2 * b * kGroupTile, *sv = sk + kGroupTile;
-    // SUB: the tile's first sub-group (of the group holding its first item)
-    const uint32_t bin0 = SUB ? (uint32_t)__umul64hi(sub.region1_M, t0) << sub.subs_log2 : 0u;
+    // SUB: the first sub-group of the tile's group
+    const uint32_t bin0 = SUB ? (uint32_t)(tile / tpg) << sub.subs_log2 : 0u;
     uint32_t k[kGroupPerThread], v[kGroupPerThread], gr[kGroupPerThread];
 #pragma unroll
     for (int u = 0; u < kGroupPerThread; ++u) {
       const uint32_t i = (uint32_t)u * kGroupThreads + tid;
-      gr[u] = 0xFFFFFFFFu;  // no item
       if (i < tn) {
         k[u] = i < tbulk ? sk[i] : __ldg(keys + t0 + i);
         v[u] = POS ? (uint32_t)(t0 + i) : (i < tbulk ? sv[i] : __ldg(values + t0 + i));
-        bool valid = true;
-        uint32_t g;
-        if constexpr (SUB) {
-          // items past their group's pairs are the unused tail of its region
-          valid = (uint32_t)(t0 + i) < __ldg(sub.ends1 + __umul64hi(sub.region1_M, t0 + i));
-          g = (k[u] == kEmptyKey ? 0u : bucket_of(tv.hf, 0, k[u]) >> sub.fine_shift) - bin0;
-        } else {
-          g = group_of(tv, k[u], shift);
-        }
-        if (valid) gr[u] = (g << 16) | atomicAdd(&cnt[g], 1u);  // group < 4096, rank < kGroupTile
+        const uint32_t g = SUB ? (k[u] == kEmptyKey ? 0u : bucket_of(tv.hf, 0, k[u]) >> sub.fine_shift) - bin0
+                               : group_of(tv, k[u], shift);
+        gr[u] = (g << 16) | atomicAdd(&cnt[g], 1u);  // group < 4096, rank < kGroupTile
       }
     }
     __syncthreads();
@@ -219,8 +226,7 @@ group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint
     uint32_t before = 0;
     for (int w = 0; w < wid; ++w) before += warp_sums[w];
     uint32_t acc = before + incl - run;
-    if (tid == kGroupThreads - 1) s_total = acc + run;  // items of the tile (the valid ones)
-    uint32_t *cur = cursors + bin0;                      // this tile's cursors
+    uint32_t *cur = cursors + bin0;  // this tile's cursors
     // reservations: with at most two groups per thread the atomics' results
     // stay in registers until after the reorder, so their round trip overlaps it
     uint32_t r0 = 0u, r1 = 0u;
@@ -241,7 +247,7 @@ group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint
     // reorder by group in place (every item of the buffer was read above)
 #pragma unroll
     for (int u = 0; u < kGroupPerThread; ++u) {
-      if (gr[u] != 0xFFFFFFFFu) {
+      if ((uint32_t)u * kGroupThreads + tid < tn) {
         const uint32_t g = gr[u] >> 16;
         const uint32_t at = pre[g] + (gr[u] & 0xFFFFu);
         sk[at] = k[u];
@@ -254,8 +260,7 @@ group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint
       if (g0 + 1 < g1) base[g0 + 1] = r1;
     }
     __syncthreads();
-    const uint32_t tv_n = SUB ? s_total : tn;
-    for (uint32_t i = tid; i < tv_n; i += kGroupThreads) {
+    for (uint32_t i = tid; i < tn; i += kGroupThreads) {
       const uint32_t g = gid[i];
       const uint32_t at = base[g] + (i - pre[g]);
       if (region && at >= (bin0 + g + 1u) * region) {  // beyond the group's region: the caller regroups exactly
@@ -333,15 +338,14 @@ cudaError_t launch_subgroup(const TableView &tv, const uint32_t *keys, const uin
                             const SubSplit &sub, uint32_t bins, uint32_t *cursors, uint32_t region, uint32_t *out_k,
                             uint32_t *out_v, cudaStream_t s) {
   if (len > 0xFFFFFFFFull || (uint64_t)bins * region > 0xFFFFFFFFull || sub.subs_log2 > 7 || region == 0 ||
-      sub.region1 < kSubgroupMinRegion)
+      sub.region1 < kSubgroupMinRegion || (sub.region1 & 7u) || sub.groups == 0)
     return cudaErrorInvalidValue;
-  static_assert(kGroupTile <= kSubgroupMinRegion, "a tile spans at most two groups");
   if ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(values)) & 15u) return cudaErrorInvalidValue;
   region_cursors_kernel<<<(bins + 255) / 256, 256, 0, s>>>(cursors, bins, region);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || len == 0) return e;
-  const uint32_t local = 2u << sub.subs_log2;  // a tile spans at most two groups
-  const uint64_t tiles = (len + kGroupTile - 1) / kGroupTile;
+  const uint32_t local = 1u << sub.subs_log2;  // a tile lies in one group
+  const uint64_t tiles = (uint64_t)sub.groups * ((sub.region1 + kGroupTile - 1) / kGroupTile);
   const size_t smem = group_scatter_smem(local);
   int blocks = 0;
   auto kern = group_scatter_kernel<false, true>;
