@@ -237,3 +237,33 @@ def test_two_level_split_and_block_placement(G, scheme, b, lf):
     assert S.build(keys, zeros if sets else vals) == 1
     gpu, cpu = st["insert_probes"] / n, S.stats.probes / n
     assert abs(gpu - cpu) <= 0.05, (gpu, cpu)
+
+
+def test_sub_group_outgrowing_its_region_falls_back(G):
+    """900 more keys than average in one 512-bucket sub-group: more than its
+    region (mean + 8 standard deviations + 64 keys, 791 above the mean here)
+    holds, and about as many as its group's region has to spare. The build
+    notices the overflow after the placement and redoes the attempt with
+    exact offsets and the filled table: same constants, a valid table,
+    bit-exact finds."""
+    n, lf, seed = 1 << 22, 0.99, 41
+    m = O.num_buckets(n, lf, 16)
+    a, c = O.derive_constants(seed, 0, 3)
+    cand = np.arange(1, 1 << 26, dtype=np.uint64)
+    h0 = ((np.uint64(a[0]) * cand + np.uint64(c[0])) % np.uint64(O.PRIME)) % np.uint64(m)
+    crowd = cand[h0 < 512][:900].astype(np.uint32)  # sub-group 0's buckets
+    assert crowd.size == 900
+    rest = W.make_keys(n + 4096, 101).numpy().view(np.uint32)
+    rest = rest[~np.isin(rest, crowd)][: n - crowd.size]
+    keys = torch.from_numpy(np.concatenate([rest, crowd]).view(np.int32).copy())
+    vals = W.make_values(n, 101)
+    t = G.HashTable("bcht", n, lf, seed=seed, group_build=1)
+    t.build(keys.cuda(), vals.cuda())
+    st = t.stats()
+    assert st["built"] == 1 and st["attempts"] == 1 and st["last_build_grouped"] == 1
+    T = O.Table(O.BCHT, n, lf, m=st["num_buckets"])
+    T.set_constants(st["hash_a"], st["hash_c"])
+    ok, msg = T.validate(keys, vals, slots=t.export())
+    assert ok, msg
+    q = W.make_queries(keys, 1 << 20, 0.5, seed=9)
+    assert (O._u32(t.find(q.cuda()).cpu()) == O.lookup(keys, vals, q)).all()
