@@ -166,7 +166,7 @@ typedef struct {
   int32_t reserved_stats;
   /* host-to-device copies of the last ght_build_host / ght_find_host call:
    * device time from its first copy's start to its last copy's end (-1 if
-   * none yet or not complete) and the bytes copied */
+   * none, as for a build read in place, or not complete) and the bytes copied */
   double last_h2d_ms;
   uint64_t last_h2d_bytes;
 } ght_stats_t;
@@ -216,10 +216,15 @@ int ght_find(const ght_table *t, const uint32_t *d_queries, uint32_t *d_out, uin
 /* As ght_build / ght_find with HOST arrays: the library stages them in
  * device memory from its own stream-ordered pool (find pipelines chunked
  * host<->device copies with the kernel) and returns when the table is built
- * or the results are in h_out. Pinned host memory copies fastest. If the
- * bounded wait for the device runs out (GHT_ERR_DEVICE_TIMEOUT, see
- * GHT_WAIT_TIMEOUT_S), copies already queued may still read h_keys/h_values
- * or write h_out afterwards. */
+ * or the results are in h_out. Pinned host memory copies fastest. A build
+ * from page-locked keys and values (allocated or registered with the CUDA
+ * runtime) that requests neither grouping nor the two-phase build
+ * (group_build and ranked_build <= 0, the host-buffer defaults) copies
+ * nothing: its input-order insert reads them in place (last_h2d_ms -1); they
+ * must stay unchanged until the call returns. If the bounded wait for the
+ * device runs out (GHT_ERR_DEVICE_TIMEOUT, see GHT_WAIT_TIMEOUT_S), copies
+ * or kernels already queued may still read h_keys/h_values or write h_out
+ * afterwards. */
 int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_values, uint64_t n);
 int ght_find_host(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out, uint64_t n);
 

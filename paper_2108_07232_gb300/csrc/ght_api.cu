@@ -531,13 +531,27 @@ int read_ctrl(const ght_table *t) {
   return wait_event(t->done);
 }
 
+// The device address of page-locked host memory (allocated or registered
+// with the CUDA runtime), or false for memory the device cannot address.
+bool device_view(const void *h, const void **d) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return false;
+  *d = a.devicePointer;
+  return true;
+}
+
 // One build from device-resident keys: fill, (group,) insert, status; retry
 // with the next attempt's constants on failure.
-int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n, uint32_t first_attempt) {
+int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n, uint32_t first_attempt,
+                 bool input_order = false) {
   t->built = false;
   t->n_stored = 0;
-  bool ranked = wants_ranked(t, n);
-  bool grouped = wants_grouping(t, n);
+  bool ranked = !input_order && wants_ranked(t, n);
+  bool grouped = !input_order && wants_grouping(t, n);
   if (grouped && ((reinterpret_cast<uintptr_t>(k) | reinterpret_cast<uintptr_t>(v ? v : k)) & 15u)) {
     // the grouping copies 16-byte pieces of the input: unaligned arrays build ungrouped
     grouped = false;
@@ -839,6 +853,19 @@ int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_value
     return fail(GHT_ERR_INVALID_ARG, "keys or values is NULL");
   if (n == 0) return build_device(t, nullptr, nullptr, 0, 0);
   if (!h_values) h_values = h_keys;  // a set ignores values
+  // Pinned host arrays the device can address: the input-order insert reads
+  // them in place, in one launch (the host link's rate is the same for the
+  // kernel's reads as for copies, and the copies' chunk pipeline -- its first
+  // chunk's wait and one insert launch tail per chunk -- goes away). A
+  // requested grouped or two-phase build still stages the pairs.
+  const void *dk_in = nullptr, *dv_in = nullptr;
+  if (t->shape.group_build <= 0 && t->shape.ranked_build <= 0 && device_view(h_keys, &dk_in) &&
+      device_view(h_values, &dv_in)) {
+    t->timed_h2d = false;  // no copies: the insert's own loads cross the host link
+    int rc = build_device(t, static_cast<const uint32_t *>(dk_in), static_cast<const uint32_t *>(dv_in), n, 0, true);
+    if (rc == GHT_OK) rc = check_duplicates(t, static_cast<const uint32_t *>(dk_in), n);
+    return rc;
+  }
   // Stage the pairs on the device (the library pool keeps the block for the
   // next call). The first attempt works on each chunk as soon as it has
   // landed, overlapping the copies with the ranked placement (two-phase

@@ -279,6 +279,35 @@ def test_host_buffer_entry_points_match_device_path(G):
     assert torch.equal(t.find(q.clone()), host_out)
 
 
+@pytest.mark.parametrize("scheme,lf", [("bcht", 0.99), ("p2bht", 0.8), ("iht", 0.86), ("cuckoo1", 0.5),
+                                       ("bcht_set", 0.99), ("bcht_lb", 0.95)])
+def test_build_in_place_from_pinned_host_memory(G, scheme, lf):
+    """Page-locked host keys and values are read in place by the input-order
+    insert (no copies: last_h2d_ms is -1); pageable ones are staged. Both
+    tables answer every query as the definitional lookup does; a requested
+    two-phase build from pinned memory still stages the pairs."""
+    n = (1 << 19) + 77
+    keys, vals = W.make_keys(n, 61), W.make_values(n, 61)
+    sets = scheme == "bcht_set"
+    q = W.make_queries(keys, 1 << 18, 0.6, seed=62)
+    want = O.lookup(keys, vals, q)
+    if sets:
+        want = (want != O.EMPTY).astype(np.uint32)
+    for src, extra in (("pinned", {}), ("pageable", {}), ("pinned", {"ranked_build": 1})):
+        if extra and scheme not in ("bcht", "bcht_set"):
+            continue
+        kk = keys.pin_memory() if src == "pinned" else keys.clone()
+        vv = vals.pin_memory() if src == "pinned" else vals.clone()
+        t = G.HashTable(scheme, n, lf, seed=63, **extra)
+        t.build(kk, None if sets else vv)
+        st = t.stats()
+        assert st["built"] == 1 and st["n_stored"] == n
+        torch.cuda.synchronize()
+        copied = st["last_h2d_ms"] > 0
+        assert copied == (src == "pageable" or bool(extra)), (src, extra, st["last_h2d_ms"])
+        assert (O._u32(t.find(q.cuda()).cpu()) == want).all(), (src, extra)
+
+
 def test_find_follows_the_current_stream(G):
     n = 30000
     t, keys, vals = build_table(G, O.BCHT, n, 0.9)
@@ -443,9 +472,10 @@ def test_duplicate_key_check(G, scheme, lf):
     if sets:
         want = (want != O.EMPTY).astype(np.uint32)
     assert (got == want).all()
-    for src in ("device", "host"):
-        kk = dup_k.cuda() if src == "device" else dup_k.pin_memory()
-        vv = None if sets else (vals.cuda() if src == "device" else vals.pin_memory())
+    place = {"device": lambda x: x.cuda(), "pinned": lambda x: x.pin_memory(), "pageable": lambda x: x.clone()}
+    for src in ("device", "pinned", "pageable"):
+        kk = place[src](dup_k)
+        vv = None if sets else place[src](vals)
         with pytest.raises(G.GhtError) as err:
             t.build(kk, vv)
         assert err.value.status == "GHT_ERR_DUPLICATE_KEY", src
