@@ -421,7 +421,8 @@ def run_ours(args, world, rank, local):
         e2e = {"value": whole_job_value(keys_per_step, args.steps, world, 1e3 * el), "unit": "Gkeys/s",
                "h2d_bytes_per_step": len(LFS) * (8 * n + 8 * n),
                "d2h_bytes_per_step": len(LFS) * 8 * n,
-               "api": "HashTable.build/find on pinned CPU tensors (ght_build_host / ght_find_host)",
+               "api": "HashTable.build/find on pinned CPU tensors (ght_build_host: the insert reads the pinned "
+                      "pairs in place; ght_find_host: pipelined copies)",
                "step_ms": step_ms,
                "call_ms": {k: round(statistics.median(v), 3) for k, v in call_ms.items()},
                "call_ms_max": {k: round(max(v), 3) for k, v in call_ms.items()},
