@@ -357,6 +357,7 @@ struct ght_table {
     // bound replaces the derived one.
     const uint64_t steps = ((uint64_t)shape.max_chain + 2ull) * (uint64_t)shape.h * ((uint64_t)shape.b + 2ull) + 64ull;
     v.max_steps = shape.max_steps ? shape.max_steps : (uint32_t)std::min<uint64_t>(steps, 0xFFFFFFF0ull);
+    v.first = 0;
     return v;
   }
 
@@ -386,8 +387,13 @@ namespace {
 // block's work cursor, which must be zero at launch (the fill clears it), so
 // that the warps finish together however long the eviction chains of their
 // keys are; a static slice per warp left a slow tail of 15-30 % at 2^28 keys.
-cudaError_t launch_insert(const ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n) {
-  const ght::TableView tv = t->view();
+// past_first: the keys are the overflow of a first-choice placement, whose
+// H_0 buckets are full (the placement counted that visit), so a BCHT insert
+// starts them at H_1 instead of reading H_0 again and exchanging there.
+cudaError_t launch_insert(const ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n,
+                          bool past_first = false) {
+  ght::TableView tv = t->view();
+  if (past_first && tv.h > 1 && (t->shape.scheme == GHT_BCHT || t->shape.scheme == GHT_BCHT_SET)) tv.first = 1;
   ght::LaunchOpts o = t->build_opts();
   o.dynamic = true;
   if (t->shape.scheme == GHT_BCHT) return ght::launch_insert_bcht(t->shape.b, tv, k, v, n, o, t->stream);
@@ -670,7 +676,7 @@ int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n,
       cudaEventRecord(t->tev[2], t->stream);
     }
     if (in > 0) {
-      e = launch_insert(t, ik, iv, in);
+      e = launch_insert(t, ik, iv, in, this_ranked);
       if (e != cudaSuccess) { rc = cuda_fail(e, "launching insert"); break; }
     }
     cudaEventRecord(t->tev[3], t->stream);
@@ -953,7 +959,7 @@ int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_value
           const uint64_t ovf = t->h_ctrl->reserved[0];
           t->place_overflow = ovf;
           if (ovf > pb.cap) retry_staged = true;  // overflow list too small: build_device falls back
-          else if (ovf > 0 && (e = launch_insert(t, pb.ovf_k, pb.ovf_v, ovf)) != cudaSuccess)
+          else if (ovf > 0 && (e = launch_insert(t, pb.ovf_k, pb.ovf_v, ovf, true)) != cudaSuccess)
             rc = cuda_fail(e, "launching insert");
         }
       }

@@ -100,6 +100,7 @@ struct TableView {
   uint32_t max_chain;  // cuckoo exchanges per insert
   uint32_t rng_seed;   // eviction xorshift seed
   uint32_t max_steps;  // per-key bound on build rounds (timeout)
+  int32_t first;       // BCHT: hash index a new key starts at (1 for keys whose H_0 is known to be full)
 };
 
 __device__ __forceinline__ uint32_t pair_key(uint64_t p) { return (uint32_t)p; }

@@ -248,7 +248,7 @@ bucketed_insert_kernel(TableView tv, const uint32_t *__restrict__ keys,
             phase[s] = 0;
             b_b[s] = 0xFFFFFFFFu;
             l_a[s] = B + 1;
-            cur[s] = bucket_of(tv.hf, 0, k);
+            cur[s] = bucket_of(tv.hf, SCHEME == kBCHT ? tv.first : 0, k);
           }
         }
       }
@@ -471,10 +471,8 @@ rank_place_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint32_
 #pragma unroll
     for (int u = 0; u < kPlacePerThread; ++u) {
       const bool fits = ok[u] && r[u] < (uint32_t)B;
-      if (fits) {
-        slots[(uint64_t)b[u] * B + r[u]] = S::make(k[u], v[u]);
-        if (COUNT) placed++;
-      }
+      if (fits) slots[(uint64_t)b[u] * B + r[u]] = S::make(k[u], v[u]);
+      if (COUNT && ok[u]) placed++;  // a visit of H_0, stored or not (the overflow insert starts at H_1)
       // overflow: one shared reservation per warp (< 2 * kPlaceTile entries
       // are staged: they are flushed below once above one tile)
       const unsigned over = __ballot_sync(kFull, ok[u] && !fits);

@@ -95,9 +95,9 @@ block_place_kernel(TableView tv, const uint32_t *__restrict__ pk, const uint32_t
         if (k[u] == kEmptyKey) continue;
         const uint32_t lb = bucket_of(tv.hf, 0, k[u]) - b0;
         const uint32_t r = atomicAdd(&bcnt[lb], 1u);
+        if (COUNT) placed++;  // a visit of H_0, stored or not (the overflow insert starts at H_1)
         if (r < (uint32_t)B) {
           img[lb * B + r] = S::make(k[u], v[u]);
-          if (COUNT) placed++;
         } else {
           const uint32_t at = atomicAdd(&s_novf, 1u);
           if (at < (uint32_t)kBPStage) {
