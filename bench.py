@@ -158,8 +158,22 @@ class ClockSampler:
 # at 2^28 keys. It describes the kernel source it was captured from,
 # identified by a hash of the find kernel's headers; after any change to them
 # the traffic is reported as null.
-FIND_TRAFFIC = {"bytes_per_launch": 60386213504, "source_sha256_16": "a0ac993b7e41992f",
+FIND_TRAFFIC = {"bytes_per_launch": 60417126976, "source_sha256_16": "1263724a61e3e7c0",
                "kernel": "bcht_find_async_kernel"}
+
+
+def build_kernels(st: dict) -> list[str]:
+    """The library kernels one build attempt launches, from the table's stats."""
+    if st["last_build_split"]:  # two grouping levels, block placement, no fill
+        return ["region_cursors_kernel", "group_scatter_kernel", "region_cursors_kernel", "group_scatter_kernel",
+                "block_place_kernel", "bucketed_insert_kernel"]
+    ks = ["fill_kernel"]
+    if st["last_build_grouped"]:  # per-group regions when placed by rank, else a count pass and prefix
+        ks += (["region_cursors_kernel"] if st["last_build_ranked"] else ["group_count_kernel", "group_scan_kernel"])
+        ks += ["group_scatter_kernel"]
+    if st["last_build_ranked"]:
+        ks += ["rank_place_kernel"]
+    return ks + ["bucketed_insert_kernel"]
 
 
 def kernel_source_hash() -> str:
@@ -330,9 +344,7 @@ def run_ours(args, world, rank, local):
             t = tables[lf]
             t.build(keys, vals)
             st = t.stats()
-            # fill + (grouping: count, scan, scatter) + (ranked placement) + cuckoo insert per attempt
-            launches[0] += (2 + (1 if st["last_build_ranked"] else 0)
-                            + (3 if st["last_build_grouped"] else 0)) * st["attempts"]
+            launches[0] += len(build_kernels(st)) * st["attempts"]
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e2 = torch.cuda.Event(enable_timing=True)
@@ -449,7 +461,6 @@ def run_ours(args, world, rank, local):
     peak, peak_src = peaks()
     kernels = {}
     st0 = tables[LFS[0]].stats()
-    ranked, grouped = bool(st0["last_build_ranked"]), bool(st0["last_build_grouped"])
     find_name = "bcht_find_async_kernel" if st0["find_staged"] else "bucketed_find_kernel"
     for lf in LFS:
         # a build's work after the fill: the grouping and the ranked placement
@@ -466,11 +477,12 @@ def run_ours(args, world, rank, local):
                                       "bytes_per_key": round(bpk, 2), "achieved_gbs": round(gbs, 1),
                                       "frac_of_hbm": round(gbs / peak, 4)}
     # dominant kernel = the kernel function with the most device time per step
-    build_name = "+".join((["group_count_kernel", "group_scatter_kernel"] if grouped else [])
-                          + (["rank_place_kernel"] if ranked else []) + ["bucketed_insert_kernel"])
+    bks = build_kernels(st0)
+    build_name = "+".join(dict.fromkeys(k for k in bks if k != "fill_kernel"))
     funcs = {find_name: [k for k in kernels if k.startswith("find")],
              build_name: [k for k in kernels if k.startswith("build")],
-             "fill_kernel": [k for k in kernels if k.startswith("fill")]}
+             # the fill, or the control block's reset when the placement writes every line
+             ("fill_kernel" if "fill_kernel" in bks else "control_reset"): [k for k in kernels if k.startswith("fill")]}
     per_func = {}
     for f, ks in funcs.items():
         t_ms = sum(kernels[k]["ms"] for k in ks)

@@ -163,7 +163,8 @@ typedef struct {
   double last_place_ms;        /* device time of its ranked placement (-1 if not two-phase) */
   uint64_t place_overflow;     /* keys the ranked placement left to the cuckoo insert */
   int32_t find_staged;         /* 1 if finds stage bucket parts in shared memory (find_async) */
-  int32_t reserved_stats;
+  int32_t last_build_split;    /* 1 if the last build split its groups into 64 KB sub-groups and placed
+                                  each whole in shared memory (block placement, no table fill) */
   /* host-to-device copies of the last ght_build_host / ght_find_host call:
    * device time from its first copy's start to its last copy's end (-1 if
    * none, as for a build read in place, or not complete) and the bytes copied */

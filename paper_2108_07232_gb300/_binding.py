@@ -52,7 +52,7 @@ class GhtStats(C.Structure):
         ("last_fill_ms", C.c_double), ("last_insert_ms", C.c_double), ("last_find_ms", C.c_double),
         ("last_group_ms", C.c_double), ("last_build_grouped", C.c_int32), ("slot_bytes", C.c_int32),
         ("last_build_ranked", C.c_int32), ("last_place_ms", C.c_double), ("place_overflow", C.c_uint64),
-        ("find_staged", C.c_int32), ("reserved_stats", C.c_int32),
+        ("find_staged", C.c_int32), ("last_build_split", C.c_int32),
         ("last_h2d_ms", C.c_double), ("last_h2d_bytes", C.c_uint64),
     ]
 

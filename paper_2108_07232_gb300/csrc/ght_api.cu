@@ -322,6 +322,7 @@ struct ght_table {
   mutable uint64_t h2d_bytes = 0;
   bool timed_build = false;
   bool last_grouped = false;
+  bool last_split = false;
   bool last_ranked = false;
   uint64_t place_overflow = 0;
   void *scratch = nullptr;  // caller-owned build scratch (ght_set_build_scratch)
@@ -682,6 +683,7 @@ int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n,
     cudaEventRecord(t->tev[3], t->stream);
     t->timed_build = true;
     t->last_grouped = grouped;
+    t->last_split = this_ranked && two_level;
     t->last_ranked = this_ranked;
     rc = read_ctrl(t);
     if (rc) break;
@@ -966,6 +968,7 @@ int ght_build_host(ght_table *t, const uint32_t *h_keys, const uint32_t *h_value
       cudaEventRecord(t->tev[3], t->stream);
       t->timed_build = true;
       t->last_grouped = false;
+      t->last_split = false;
       t->last_ranked = ranked && !retry_staged;
       if (rc == GHT_OK && !retry_staged) rc = read_ctrl(t);
       if (rc == GHT_OK && !retry_staged) {
@@ -1128,6 +1131,7 @@ int ght_stats(const ght_table *t, ght_stats_t *out) {
   float ms = 0.f;
   out->last_group_ms = -1.0;
   out->last_build_grouped = t->last_grouped ? 1 : 0;
+  out->last_build_split = t->last_split ? 1 : 0;
   out->slot_bytes = t->shape.slot_bytes;
   out->last_build_ranked = t->last_ranked ? 1 : 0;
   out->last_place_ms = -1.0;

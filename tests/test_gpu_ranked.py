@@ -61,6 +61,7 @@ def test_two_phase_and_cuckoo_only_builds(G, b, lf, group, ranked):
     want_ranked = ranked > 0 or (ranked == 0 and group > 0)
     assert st["last_build_ranked"] == int(want_ranked)
     assert st["last_build_grouped"] == int(group > 0)
+    assert st["last_build_split"] in ((0, 1) if want_ranked and group > 0 else (0,))
     if want_ranked:
         assert st["last_place_ms"] >= 0.0
         assert (st["last_group_ms"] >= 0.0) == (group > 0)
@@ -214,6 +215,7 @@ def test_two_level_split_and_block_placement(G, scheme, b, lf):
     t.build(keys.cuda(), None if sets else vals.cuda())
     st = t.stats()
     assert st["built"] == 1 and st["last_build_ranked"] == 1 and st["last_build_grouped"] == 1
+    assert st["last_build_split"] == 1
     T = O.Table(O.BCHT, n, lf, b=b, m=st["num_buckets"])
     T.set_constants(st["hash_a"], st["hash_c"])
     raw = t.export()
@@ -261,6 +263,7 @@ def test_sub_group_outgrowing_its_region_falls_back(G):
     t.build(keys.cuda(), vals.cuda())
     st = t.stats()
     assert st["built"] == 1 and st["attempts"] == 1 and st["last_build_grouped"] == 1
+    assert st["last_build_split"] == 0  # the redone attempt placed with exact offsets
     T = O.Table(O.BCHT, n, lf, m=st["num_buckets"])
     T.set_constants(st["hash_a"], st["hash_c"])
     ok, msg = T.validate(keys, vals, slots=t.export())
