@@ -112,13 +112,15 @@ typedef struct {
    * (ght_build_scratch_bytes), else the build runs the cuckoo insert for
    * every key. */
   int32_t ranked_build;
-  /* Finds of 128-byte buckets (BCHT with 16 pairs and 4-lane tiles; the
-   * keys-only set, whose find tiles then have 4 lanes): 1 = stage the bucket
-   * parts in shared memory with asynchronous copies, keys_per_lane (2..8,
-   * default 6) query sets in flight per lane; -1 = off (bucket parts in
-   * registers, keys_per_lane 1..2); 0 = default: on where it applies, the
-   * table's slots take at least the device's L2 size and keys_per_lane is
-   * not given as 1. Other shapes reject 1. */
+  /* Finds of 128-byte buckets (16 pairs: BCHT with 4-lane tiles, P2BHT, IHT
+   * and the load-balanced BCHT, whose find tiles then have 4 lanes; the
+   * keys-only set, likewise): 1 = stage the bucket parts in shared memory
+   * with asynchronous copies, keys_per_lane (2..8, default 6) query sets in
+   * flight per lane, each scheme's own probe order and stop rule; -1 = off
+   * (bucket parts in registers, keys_per_lane 1..2); 0 = default: on where
+   * it applies, the table's slots take at least the device's L2 size and
+   * neither keys_per_lane 1 nor (except for BCHT's 4) tile_lanes is given.
+   * Other shapes (32-pair buckets, CUCKOO1) reject 1. */
   int32_t find_async;
   /* 1: after a successful ght_build / ght_build_host, check that no input key
    * is stored more than once (every candidate bucket of every input key is

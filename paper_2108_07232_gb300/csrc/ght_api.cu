@@ -137,14 +137,15 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
       if (!ok) return fail(GHT_ERR_INVALID_ARG, "tile of %d lanes unsupported for bucket size %d", g, b);
     }
   }
-  // the staged find reads 128-byte buckets (BCHT with 16 pairs, the set with
-  // 32 keys) with 4-lane tiles; the set's default 8-lane find tile gives way
-  // to it unless tile_lanes is given
+  // the staged find reads 128-byte buckets (16 pairs of BCHT, P2BHT, IHT and
+  // the load-balanced BCHT; 32 keys of the set) with 4-lane tiles; the
+  // default 8-lane find tile of the schemes other than BCHT gives way to it
+  // unless tile_lanes is given
   const bool user_tile = user && user->tile_lanes;
-  const bool staged_bucket = (scheme == GHT_BCHT && b == 16) || scheme == GHT_BCHT_SET;
-  const bool staged_shape = staged_bucket && (d.tile_lanes == 4 || (scheme == GHT_BCHT_SET && !user_tile));
+  const bool staged_bucket = (b == 16 && scheme != GHT_CUCKOO1) || scheme == GHT_BCHT_SET;
+  const bool staged_shape = staged_bucket && (d.tile_lanes == 4 || (scheme != GHT_BCHT && !user_tile));
   if (d.find_async > 0 && !staged_shape)
-    return fail(GHT_ERR_INVALID_ARG, "the staged find is for 128-byte buckets (BCHT b = 16, the set) and 4-lane tiles");
+    return fail(GHT_ERR_INVALID_ARG, "the staged find is for 128-byte buckets (16 pairs, the set) and 4-lane tiles");
   if (d.build_keys_per_lane != 1 && d.build_keys_per_lane != 2)
     return fail(GHT_ERR_INVALID_ARG, "keys per lane must be 1 or 2");
   if (scheme == GHT_IHT && (d.threshold < 1 || d.threshold > b + 1))
@@ -526,7 +527,9 @@ cudaError_t launch_find(const ght_table *t, const uint32_t *q, uint32_t *out, ui
     return o.async_find ? ght::launch_find_set_async(tv, q, out, n, o, t->stream)
                         : ght::launch_find_set(tv, q, out, n, o, t->stream);
   }
-  return ght::launch_find_other(t->shape.scheme, t->shape.b, tv, q, out, n, t->find_opts(), t->stream);
+  const ght::LaunchOpts o = t->find_opts();
+  if (o.async_find) return ght::launch_find_bcht_async(t->shape.b, tv, q, out, n, o, t->stream, false);
+  return ght::launch_find_other(t->shape.scheme, t->shape.b, tv, q, out, n, o, t->stream);
 }
 
 // Read the control block after the stream's work; bounded wait.

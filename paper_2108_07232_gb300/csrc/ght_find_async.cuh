@@ -1,9 +1,13 @@
-// ght_find_async.cuh -- BCHT bulk find with bucket parts staged in shared
-// memory by asynchronous copies (cp.async), for 128-byte buckets (16 pairs,
-// or 32 keys of the keys-only set) read by 4-lane tiles.
+// ght_find_async.cuh -- bulk find of the bucketed tables with bucket parts
+// staged in shared memory by asynchronous copies (cp.async), for 128-byte
+// buckets (16 pairs, or 32 keys of the keys-only set) read by 4-lane tiles.
 //
-// The probe order, early exit and tile evaluation are those of
-// bucketed_find_kernel (Sec. V-B find). The difference is where a bucket in
+// The probe order, stop rules and tile evaluation are those of
+// bucketed_find_kernel: every scheme probes H_0, H_1, ... and stops at the
+// bucket holding the key; BCHT (and the set) also stops at a bucket with an
+// empty slot (Sec. V-B find), P2BHT, IHT and the load-balanced BCHT read on
+// until the last candidate (Sec. V-C, V-D: no early exit), which the
+// early_exit argument selects. The difference is where a bucket in
 // flight lives: there, in registers (32 per query set and lane), which caps
 // a lane at two sets, evaluated one step after their reads are issued; here,
 // in the warp's shared memory, so a lane keeps KPL sets in flight and a set
@@ -41,7 +45,7 @@ constexpr size_t find_async_smem_per_warp() {
 template <int KPL, int WARPS, bool COUNT, typename S = PairSlot>
 __global__ void __launch_bounds__(32 * WARPS)
 bcht_find_async_kernel(TableView tv, const uint32_t *__restrict__ queries, uint32_t *__restrict__ out, uint64_t n,
-                       uint64_t per_warp) {
+                       uint64_t per_warp, bool early_exit) {
   constexpr int G = 4;
   constexpr bool kPairs = sizeof(typename S::T) == 8;  // else 32-bit keys (a set)
   static_assert(KPL >= 2 && KPL <= 8, "query sets in flight");
@@ -168,7 +172,7 @@ bcht_find_async_kernel(TableView tv, const uint32_t *__restrict__ queries, uint3
           if (my_hit) {
             result = my_val;
             finish = true;
-          } else if (my_emp) {
+          } else if (early_exit && my_emp) {
             finish = true;
           } else if (++probe[e] >= tv.h) {
             finish = true;
@@ -205,7 +209,7 @@ bcht_find_async_kernel(TableView tv, const uint32_t *__restrict__ queries, uint3
 // multiple of the SM's four schedulers (6 sets: 4 blocks, 8 warps per SM).
 template <int KPL, int WARPS, typename S>
 inline cudaError_t launch_staged_find(const TableView &tv, const uint32_t *q, uint32_t *out, uint64_t n, bool count,
-                                      int blocks_per_sm, cudaStream_t s) {
+                                      int blocks_per_sm, bool early_exit, cudaStream_t s) {
   auto kern = count ? bcht_find_async_kernel<KPL, WARPS, true, S> : bcht_find_async_kernel<KPL, WARPS, false, S>;
   constexpr int kBlock = 32 * WARPS;
   const size_t smem = WARPS * find_async_smem_per_warp<KPL>();
@@ -213,22 +217,23 @@ inline cudaError_t launch_staged_find(const TableView &tv, const uint32_t *q, ui
   cudaError_t e = grid_for_smem(kern, kBlock, smem, n, blocks_per_sm, &blocks);
   if (e != cudaSuccess) return e;
   const uint64_t warps = (uint64_t)blocks * WARPS;
-  kern<<<blocks, kBlock, smem, s>>>(tv, q, out, n, (n + warps - 1) / warps);
+  kern<<<blocks, kBlock, smem, s>>>(tv, q, out, n, (n + warps - 1) / warps, early_exit);
   return cudaGetLastError();
 }
 
 // keys_per_lane = sets in flight, 2..8
 template <typename S>
 inline cudaError_t launch_staged_find_kpl(const TableView &tv, const uint32_t *q, uint32_t *out, uint64_t n,
-                                          int keys_per_lane, bool count, int blocks_per_sm, cudaStream_t s) {
+                                          int keys_per_lane, bool count, int blocks_per_sm, bool early_exit,
+                                          cudaStream_t s) {
   switch (keys_per_lane) {
-    case 2: return launch_staged_find<2, 4, S>(tv, q, out, n, count, blocks_per_sm, s);
-    case 3: return launch_staged_find<3, 4, S>(tv, q, out, n, count, blocks_per_sm, s);
-    case 4: return launch_staged_find<4, 4, S>(tv, q, out, n, count, blocks_per_sm, s);
-    case 5: return launch_staged_find<5, 2, S>(tv, q, out, n, count, blocks_per_sm, s);
-    case 6: return launch_staged_find<6, 2, S>(tv, q, out, n, count, blocks_per_sm, s);
-    case 7: return launch_staged_find<7, 2, S>(tv, q, out, n, count, blocks_per_sm, s);
-    case 8: return launch_staged_find<8, 2, S>(tv, q, out, n, count, blocks_per_sm, s);
+    case 2: return launch_staged_find<2, 4, S>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
+    case 3: return launch_staged_find<3, 4, S>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
+    case 4: return launch_staged_find<4, 4, S>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
+    case 5: return launch_staged_find<5, 2, S>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
+    case 6: return launch_staged_find<6, 2, S>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
+    case 7: return launch_staged_find<7, 2, S>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
+    case 8: return launch_staged_find<8, 2, S>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -132,8 +132,10 @@ cudaError_t launch_insert_bcht(int B, const TableView &tv, const uint32_t *k, co
                                uint64_t n, const LaunchOpts &o, cudaStream_t s);
 cudaError_t launch_find_bcht(int B, const TableView &tv, const uint32_t *q, uint32_t *out,
                              uint64_t n, const LaunchOpts &o, cudaStream_t s);
+// The staged find of 16-pair buckets; early_exit = false gives the stop rule
+// of P2BHT, IHT and the load-balanced BCHT (read on until the key is found).
 cudaError_t launch_find_bcht_async(int B, const TableView &tv, const uint32_t *q, uint32_t *out, uint64_t n,
-                                   const LaunchOpts &o, cudaStream_t s);
+                                   const LaunchOpts &o, cudaStream_t s, bool early_exit = true);
 cudaError_t launch_find_set_async(const TableView &tv, const uint32_t *q, uint32_t *out, uint64_t n,
                                   const LaunchOpts &o, cudaStream_t s);
 bool bcht_shape_supported(int B, int G);

@@ -64,7 +64,7 @@ cudaError_t launch_find_set(const TableView &tv, const uint32_t *q, uint32_t *ou
 cudaError_t launch_find_set_async(const TableView &tv, const uint32_t *q, uint32_t *out, uint64_t n,
                                   const LaunchOpts &o, cudaStream_t s) {
   if (o.tile_lanes != 4) return cudaErrorInvalidValue;
-  return launch_staged_find_kpl<KeySlot>(tv, q, out, n, o.keys_per_lane, o.count, o.blocks_per_sm, s);
+  return launch_staged_find_kpl<KeySlot>(tv, q, out, n, o.keys_per_lane, o.count, o.blocks_per_sm, true, s);
 }
 
 }  // namespace ght
