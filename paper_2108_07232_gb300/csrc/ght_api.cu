@@ -137,15 +137,16 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
       if (!ok) return fail(GHT_ERR_INVALID_ARG, "tile of %d lanes unsupported for bucket size %d", g, b);
     }
   }
-  // the staged find reads 128-byte buckets (16 pairs of BCHT, P2BHT, IHT and
-  // the load-balanced BCHT; 32 keys of the set) with 4-lane tiles; the
-  // default 8-lane find tile of the schemes other than BCHT gives way to it
-  // unless tile_lanes is given
+  // the staged find reads buckets of 16 or 32 pairs (BCHT, P2BHT, IHT, the
+  // load-balanced BCHT) or 32 keys (the set) with 4-lane tiles; a default
+  // find tile of another width gives way to it unless tile_lanes is given
   const bool user_tile = user && user->tile_lanes;
-  const bool staged_bucket = (b == 16 && scheme != GHT_CUCKOO1) || scheme == GHT_BCHT_SET;
-  const bool staged_shape = staged_bucket && (d.tile_lanes == 4 || (scheme != GHT_BCHT && !user_tile));
+  const bool staged_bucket = scheme != GHT_CUCKOO1;
+  const bool staged_shape = staged_bucket && (d.tile_lanes == 4 || !user_tile);
   if (d.find_async > 0 && !staged_shape)
-    return fail(GHT_ERR_INVALID_ARG, "the staged find is for 128-byte buckets (16 pairs, the set) and 4-lane tiles");
+    return fail(GHT_ERR_INVALID_ARG, "the staged find is for bucketed tables with 4-lane tiles");
+  const bool two_lines = scheme != GHT_BCHT_SET && b == 32;  // 256-byte buckets
+  const int max_sets = two_lines ? 6 : 8;
   if (d.build_keys_per_lane != 1 && d.build_keys_per_lane != 2)
     return fail(GHT_ERR_INVALID_ARG, "keys per lane must be 1 or 2");
   if (scheme == GHT_IHT && (d.threshold < 1 || d.threshold > b + 1))
@@ -157,19 +158,19 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
   // The staged find by default where it applies and the slots do not fit in
   // the L2: there its deeper pipeline hides DRAM latency; on an L2-resident
   // table the register find's higher occupancy wins. A given keys_per_lane of
-  // 1 keeps the register find. 6 query sets in flight unless keys_per_lane is
-  // given.
+  // 1 keeps the register find. 6 query sets in flight (3 for 256-byte
+  // buckets) unless keys_per_lane is given.
   const uint64_t slot_bytes = scheme == GHT_BCHT_SET ? 4 : 8;
   const bool kpl_given = user && user->keys_per_lane;
   const bool async_find =
       d.find_async > 0 || (d.find_async == 0 && staged_shape && !(kpl_given && d.keys_per_lane < 2) &&
                            (uint64_t)want * b * slot_bytes >= device_l2_bytes());
-  if (async_find && !kpl_given) d.keys_per_lane = 6;
+  if (async_find && !kpl_given) d.keys_per_lane = two_lines ? 3 : 6;
   if (async_find) d.tile_lanes = 4;
   if (!async_find && scheme == GHT_BCHT_SET && d.tile_lanes == 4)
     return fail(GHT_ERR_INVALID_ARG, "4-lane find tiles of the set need the staged find");
-  if (async_find ? (d.keys_per_lane < 2 || d.keys_per_lane > 8) : (d.keys_per_lane != 1 && d.keys_per_lane != 2))
-    return fail(GHT_ERR_INVALID_ARG, "keys per lane must be 1 or 2 (2 to 8 for the staged find)");
+  if (async_find ? (d.keys_per_lane < 2 || d.keys_per_lane > max_sets) : (d.keys_per_lane != 1 && d.keys_per_lane != 2))
+    return fail(GHT_ERR_INVALID_ARG, "keys per lane must be 1 or 2 (2 to %d for the staged find)", max_sets);
   s->scheme = scheme;
   s->b = b;
   s->h = h;

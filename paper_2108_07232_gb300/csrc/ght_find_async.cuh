@@ -33,30 +33,42 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // Shared memory per warp: KPL sets x 32 buckets (one per lane of the warp as
-// owner) x 8 chunks of 16 bytes. Lane r of a tile holds chunks 2r and 2r + 1
-// of each of its tile's buckets; chunk c of the bucket of owner lane o is
-// stored at chunk position c ^ (o >> 2 & 7), so the eight tiles of a warp
-// read different bank groups.
-template <int KPL>
+// owner) x 8 LINES chunks of 16 bytes (LINES = 128-byte lines per bucket).
+// One line: lane r of a tile holds chunks 2r and 2r + 1 of each of its
+// tile's buckets, and chunk c of the bucket of owner lane o is stored at
+// chunk position c ^ (o >> 2 & 7), so the eight tiles of a warp read
+// different bank groups. Two lines (32 pairs): lane r holds chunks r + 4i,
+// i < 4, at position c ^ 4 (o >> 2 & 1): the two tiles that share a quarter
+// of the warp's 16-byte accesses then cover the eight bank groups once.
+template <int KPL, int LINES = 1>
 constexpr size_t find_async_smem_per_warp() {
-  return (size_t)KPL * 32 * 8 * 16;
+  return (size_t)KPL * 32 * 8 * LINES * 16;
 }
 
-template <int KPL, int WARPS, bool COUNT, typename S = PairSlot>
+template <int LINES>
+__device__ __forceinline__ unsigned staged_chunk(int r, int i) {
+  return LINES == 1 ? (unsigned)(2 * r + i) : (unsigned)(r + 4 * i);
+}
+
+template <int KPL, int WARPS, bool COUNT, typename S = PairSlot, int LINES = 1>
 __global__ void __launch_bounds__(32 * WARPS)
 bcht_find_async_kernel(TableView tv, const uint32_t *__restrict__ queries, uint32_t *__restrict__ out, uint64_t n,
                        uint64_t per_warp, bool early_exit) {
   constexpr int G = 4;
   constexpr bool kPairs = sizeof(typename S::T) == 8;  // else 32-bit keys (a set)
+  constexpr int kChunks = 8 * LINES;                   // 16-byte chunks per bucket
+  constexpr int kPerLane = kChunks / G;                // chunks a tile lane copies and evaluates
   static_assert(KPL >= 2 && KPL <= 8, "query sets in flight");
+  static_assert(LINES == 1 || (LINES == 2 && kPairs), "one-line buckets, or 32-pair buckets");
   extern __shared__ uint4 fa_smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int r = lane & (G - 1);
   const int tbase = lane - r;
-  const unsigned swz = (unsigned)(lane >> 2) & 7u;  // this tile's chunk swizzle
+  // this tile's chunk swizzle
+  const unsigned swz = LINES == 1 ? ((unsigned)(lane >> 2) & 7u) : (((unsigned)(lane >> 2) & 1u) << 2);
   const unsigned tmask = ((1u << G) - 1u) << tbase;
-  uint4 *wbuf = fa_smem + (size_t)wib * KPL * 32 * 8;
+  uint4 *wbuf = fa_smem + (size_t)wib * KPL * 32 * kChunks;
   const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t beg = warp * per_warp;
   if (beg >= n) return;  // whole warp
@@ -102,17 +114,20 @@ bcht_find_async_kernel(TableView tv, const uint32_t *__restrict__ queries, uint3
       act[s] = __ballot_sync(kFull, active[s]);
       if (act[s] != 0u) {
         const uint32_t myb = active[s] ? bucket_of(tv.hf, probe[s], key[s]) : 0u;
-        uint4 *sbuf = wbuf + (size_t)s * 32 * 8;
+        uint4 *sbuf = wbuf + (size_t)s * 32 * kChunks;
 #pragma unroll
         for (int j = 0; j < G; ++j) {
           const int owner = tbase + j;
           const uint32_t bj = __shfl_sync(kFull, myb, owner);
           if ((act[s] >> owner) & 1u) {
-            // 32 bytes of the 128-byte bucket: pairs [4r, 4r + 4) or keys [8r, 8r + 8)
-            const uint4 *src = reinterpret_cast<const uint4 *>(tv.slots) + (uint64_t)bj * 8 + 2 * r;
-            uint4 *row = sbuf + owner * 8;
-            cp_async16(row + ((2u * r) ^ swz), src);
-            cp_async16(row + ((2u * r + 1u) ^ swz), src + 1);
+            // this lane's quarter of the bucket (one line: pairs [4r, 4r + 4) or keys [8r, 8r + 8))
+            const uint4 *src = reinterpret_cast<const uint4 *>(tv.slots) + (uint64_t)bj * kChunks;
+            uint4 *row = sbuf + owner * kChunks;
+#pragma unroll
+            for (int i = 0; i < kPerLane; ++i) {
+              const unsigned c = staged_chunk<LINES>(r, i);
+              cp_async16(row + (c ^ swz), src + c);
+            }
           }
         }
       }
@@ -123,7 +138,7 @@ bcht_find_async_kernel(TableView tv, const uint32_t *__restrict__ queries, uint3
       cp_async_wait<KPL - 1>();
       __syncwarp();  // the other lanes' copies of set e are visible
       if (act[e] != 0u) {
-        const uint4 *ebuf = wbuf + (size_t)e * 32 * 8;
+        const uint4 *ebuf = wbuf + (size_t)e * 32 * kChunks;
         bool my_hit = false, my_emp = false;
         uint32_t my_val = S::missing();
 #pragma unroll
@@ -134,19 +149,23 @@ bcht_find_async_kernel(TableView tv, const uint32_t *__restrict__ queries, uint3
           bool hit = false, emp = false;
           uint32_t hv = 0u;
           if (aj) {
-            const uint4 *row = ebuf + owner * 8;
-            const uint4 c0 = row[(2u * r) ^ swz], c1 = row[(2u * r + 1u) ^ swz];
+            const uint4 *row = ebuf + owner * kChunks;
             if constexpr (kPairs) {
-              const uint32_t ks[4] = {c0.x, c0.z, c1.x, c1.z}, vs[4] = {c0.y, c0.w, c1.y, c1.w};
 #pragma unroll
-              for (int p = 0; p < 4; ++p) {
-                if (ks[p] == kj) {
+              for (int i = 0; i < kPerLane; ++i) {
+                const uint4 c = row[staged_chunk<LINES>(r, i) ^ swz];  // pairs (c.x, c.y), (c.z, c.w)
+                if (c.x == kj) {
                   hit = true;
-                  hv = vs[p];
+                  hv = c.y;
                 }
-                emp |= ks[p] == kEmptyKey;
+                if (c.z == kj) {
+                  hit = true;
+                  hv = c.w;
+                }
+                emp |= c.x == kEmptyKey || c.z == kEmptyKey;
               }
             } else {
+              const uint4 c0 = row[(2u * r) ^ swz], c1 = row[(2u * r + 1u) ^ swz];
               const uint32_t ks[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
 #pragma unroll
               for (int p = 0; p < 8; ++p) {
@@ -205,14 +224,16 @@ bcht_find_async_kernel(TableView tv, const uint32_t *__restrict__ queries, uint3
 
 // Launch with KPL sets in flight and WARPS warps per block, as many blocks
 // as are resident at once (shared memory sets the residency, KPL x 4 KB per
-// warp); 2-warp blocks for the deep pipelines keep the resident warps a
-// multiple of the SM's four schedulers (6 sets: 4 blocks, 8 warps per SM).
-template <int KPL, int WARPS, typename S>
+// warp and bucket line); 2-warp blocks for the deep pipelines keep the
+// resident warps a multiple of the SM's four schedulers (6 sets of one-line
+// buckets: 4 blocks, 8 warps per SM).
+template <int KPL, int WARPS, typename S, int LINES = 1>
 inline cudaError_t launch_staged_find(const TableView &tv, const uint32_t *q, uint32_t *out, uint64_t n, bool count,
                                       int blocks_per_sm, bool early_exit, cudaStream_t s) {
-  auto kern = count ? bcht_find_async_kernel<KPL, WARPS, true, S> : bcht_find_async_kernel<KPL, WARPS, false, S>;
+  auto kern = count ? bcht_find_async_kernel<KPL, WARPS, true, S, LINES>
+                    : bcht_find_async_kernel<KPL, WARPS, false, S, LINES>;
   constexpr int kBlock = 32 * WARPS;
-  const size_t smem = WARPS * find_async_smem_per_warp<KPL>();
+  const size_t smem = WARPS * find_async_smem_per_warp<KPL, LINES>();
   int blocks = 0;
   cudaError_t e = grid_for_smem(kern, kBlock, smem, n, blocks_per_sm, &blocks);
   if (e != cudaSuccess) return e;
@@ -221,20 +242,32 @@ inline cudaError_t launch_staged_find(const TableView &tv, const uint32_t *q, ui
   return cudaGetLastError();
 }
 
-// keys_per_lane = sets in flight, 2..8
-template <typename S>
+// keys_per_lane = sets in flight: 2..8 for one-line buckets, 2..6 for
+// two-line buckets (8 KB per set and warp)
+template <typename S, int LINES = 1>
 inline cudaError_t launch_staged_find_kpl(const TableView &tv, const uint32_t *q, uint32_t *out, uint64_t n,
                                           int keys_per_lane, bool count, int blocks_per_sm, bool early_exit,
                                           cudaStream_t s) {
-  switch (keys_per_lane) {
-    case 2: return launch_staged_find<2, 4, S>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
-    case 3: return launch_staged_find<3, 4, S>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
-    case 4: return launch_staged_find<4, 4, S>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
-    case 5: return launch_staged_find<5, 2, S>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
-    case 6: return launch_staged_find<6, 2, S>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
-    case 7: return launch_staged_find<7, 2, S>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
-    case 8: return launch_staged_find<8, 2, S>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
-    default: return cudaErrorInvalidValue;
+  if constexpr (LINES == 2) {
+    switch (keys_per_lane) {
+      case 2: return launch_staged_find<2, 4, S, LINES>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
+      case 3: return launch_staged_find<3, 4, S, LINES>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
+      case 4: return launch_staged_find<4, 2, S, LINES>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
+      case 5: return launch_staged_find<5, 2, S, LINES>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
+      case 6: return launch_staged_find<6, 2, S, LINES>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    switch (keys_per_lane) {
+      case 2: return launch_staged_find<2, 4, S, LINES>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
+      case 3: return launch_staged_find<3, 4, S, LINES>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
+      case 4: return launch_staged_find<4, 4, S, LINES>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
+      case 5: return launch_staged_find<5, 2, S, LINES>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
+      case 6: return launch_staged_find<6, 2, S, LINES>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
+      case 7: return launch_staged_find<7, 2, S, LINES>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
+      case 8: return launch_staged_find<8, 2, S, LINES>(tv, q, out, n, count, blocks_per_sm, early_exit, s);
+      default: return cudaErrorInvalidValue;
+    }
   }
 }
 

@@ -62,8 +62,12 @@ cudaError_t launch_place_bcht(int B, const TableView &tv, const uint32_t *k, con
 
 cudaError_t launch_find_bcht_async(int B, const TableView &tv, const uint32_t *q, uint32_t *out, uint64_t n,
                                    const LaunchOpts &o, cudaStream_t s, bool early_exit) {
-  if (B != 16 || o.tile_lanes != 4) return cudaErrorInvalidValue;
-  return launch_staged_find_kpl<PairSlot>(tv, q, out, n, o.keys_per_lane, o.count, o.blocks_per_sm, early_exit, s);
+  if (o.tile_lanes != 4) return cudaErrorInvalidValue;
+  if (B == 16)
+    return launch_staged_find_kpl<PairSlot, 1>(tv, q, out, n, o.keys_per_lane, o.count, o.blocks_per_sm, early_exit, s);
+  if (B == 32)
+    return launch_staged_find_kpl<PairSlot, 2>(tv, q, out, n, o.keys_per_lane, o.count, o.blocks_per_sm, early_exit, s);
+  return cudaErrorInvalidValue;
 }
 
 bool bcht_shape_supported(int B, int G) {

@@ -88,13 +88,18 @@ def test_staged_find_shapes(L):
     assert L.ght_table_bytes(0, 1000, 0.9, {"find_async": 1, "keys_per_lane": 9}) == 0
     assert L.ght_table_bytes(0, 1000, 0.9, {"find_async": 1, "tile_lanes": 16}) == 0
     assert L.ght_table_bytes(0, 1000, 0.9, {"find_async": 1, "bucket_size": 32, "tile_lanes": 8}) == 0
-    for scheme in (1, 2, 4):  # P2BHT, IHT, load-balanced BCHT: 16-pair buckets only, 4-lane tiles
-        base = L.ght_table_bytes(scheme, 1000, 0.8)
-        assert L.ght_table_bytes(scheme, 1000, 0.8, {"find_async": 1}) == base
-        assert L.ght_table_bytes(scheme, 1000, 0.8, {"find_async": 1, "keys_per_lane": 8}) == base
-        assert L.ght_table_bytes(scheme, 1000, 0.8, {"find_async": 1, "bucket_size": 32}) == 0
-        assert L.ght_table_bytes(scheme, 1000, 0.8, {"find_async": 1, "tile_lanes": 8}) == 0
-        assert L.ght_table_bytes(scheme, 1000, 0.8, {"tile_lanes": 4}) == 0  # register find: 8-lane tiles
+    for scheme in (0, 1, 2, 4):  # BCHT, P2BHT, IHT, load-balanced BCHT; 4-lane tiles
+        for b, most in ((16, 8), (32, 6)):  # sets in flight: 2..8, or 2..6 for 256-byte buckets
+            base = L.ght_table_bytes(scheme, 1000, 0.8, {"bucket_size": b})
+            assert base > 0
+            assert L.ght_table_bytes(scheme, 1000, 0.8, {"find_async": 1, "bucket_size": b}) == base
+            assert L.ght_table_bytes(scheme, 1000, 0.8, {"find_async": 1, "bucket_size": b,
+                                                         "keys_per_lane": most}) == base
+            assert L.ght_table_bytes(scheme, 1000, 0.8, {"find_async": 1, "bucket_size": b,
+                                                         "keys_per_lane": most + 1}) == 0
+            assert L.ght_table_bytes(scheme, 1000, 0.8, {"find_async": 1, "bucket_size": b, "tile_lanes": 8}) == 0
+        if scheme:
+            assert L.ght_table_bytes(scheme, 1000, 0.8, {"tile_lanes": 4}) == 0  # register find: 8-lane tiles
     assert L.ght_table_bytes(3, 1000, 0.8, {"find_async": 1}) == 0  # 1CHT
     # the register find keeps 1..2 sets per lane
     assert L.ght_table_bytes(0, 1000, 0.9, {"find_async": -1, "keys_per_lane": 3}) == 0

@@ -416,21 +416,26 @@ def test_staged_find_parity(G, kpl, lf):
     with pytest.raises(G.GhtError):
         G.HashTable("bcht", 1000, 0.9, find_async=1, tile_lanes=8)
     with pytest.raises(G.GhtError):
-        G.HashTable("p2bht", 1000, 0.8, find_async=1, bucket_size=32)
+        G.HashTable("cuckoo1", 1000, 0.5, find_async=1)
+    with pytest.raises(G.GhtError):
+        G.HashTable("p2bht", 1000, 0.8, find_async=1, bucket_size=32, keys_per_lane=7)
     with pytest.raises(G.GhtError):
         G.HashTable("bcht", 1000, 0.9, find_async=1, keys_per_lane=9)
 
 
-@pytest.mark.parametrize("kpl", [2, 6])
-@pytest.mark.parametrize("scheme,lf", [(O.P2BHT, 0.8), (O.IHT, 0.86), (O.BCHT_LB, 0.95), (O.BCHT_LB, 0.99)])
-def test_staged_find_parity_without_early_exit(G, scheme, lf, kpl):
-    """P2BHT, IHT and the load-balanced BCHT through the staged find (their
-    stop rule: a hit ends the probe sequence, an empty slot does not; Sec.
-    V-C, V-D): results bit-exact against the definitional lookup at f = 0,
-    0.5, 1 and on sentinel queries and a ragged tail; probe counts equal to
-    the oracle's on the GPU's own table (P2BHT negatives read 2 buckets, IHT
-    and load-balanced negatives 3)."""
-    t, keys, vals = build_table(G, scheme, N_SMALL, lf, find_async=1, keys_per_lane=kpl)
+@pytest.mark.parametrize("kpl", [2, 3, 6])
+@pytest.mark.parametrize("scheme,b,lf", [(O.P2BHT, 16, 0.8), (O.IHT, 16, 0.86), (O.BCHT_LB, 16, 0.95),
+                                         (O.BCHT_LB, 16, 0.99), (O.P2BHT, 32, 0.9), (O.IHT, 32, 0.9),
+                                         (O.BCHT_LB, 32, 0.99), (O.BCHT, 32, 0.99), (O.BCHT, 32, 0.9)])
+def test_staged_find_parity_each_scheme(G, scheme, b, lf, kpl):
+    """The staged find for P2BHT, IHT and the load-balanced BCHT (their stop
+    rule: a hit ends the probe sequence, an empty slot does not; Sec. V-C,
+    V-D) and for every scheme with 32-pair (two-line) buckets: results
+    bit-exact against the definitional lookup at f = 0, 0.5, 1 and on
+    sentinel queries and a ragged tail; probe counts equal to the oracle's on
+    the GPU's own table (negatives: P2BHT 2 buckets, IHT and load-balanced
+    3; BCHT as the oracle evaluates its early exit)."""
+    t, keys, vals = build_table(G, scheme, N_SMALL, lf, find_async=1, keys_per_lane=kpl, bucket_size=b)
     st = t.stats()
     assert (st["find_staged"], st["keys_per_lane"], st["tile_lanes"]) == (1, kpl, 4)
     T = oracle_view(st, scheme, N_SMALL, lf)
@@ -446,7 +451,8 @@ def test_staged_find_parity_without_early_exit(G, scheme, lf, kpl):
     neg = W.make_negatives(N_SMALL, 4099, 1)
     t.reset_counters()
     assert (O._u32(t.find(neg.cuda()).cpu()) == O.EMPTY).all()
-    assert t.stats()["find_probes"] == (2 if scheme == O.P2BHT else 3) * 4099
+    want_probes = T.find(neg, slots=slots)[2] if scheme == O.BCHT else (2 if scheme == O.P2BHT else 3) * 4099
+    assert t.stats()["find_probes"] == want_probes
     q = torch.cat([keys[:5], torch.tensor([-1, -1], dtype=torch.int32), W.make_negatives(N_SMALL, 3, 1)])
     assert (O._u32(t.find(q.cuda()).cpu()) == O.lookup(keys, vals, q)).all()
 
@@ -479,9 +485,10 @@ def test_staged_find_is_the_bcht_default(G):
     for s in ("p2bht", "iht", "bcht_lb", "cuckoo1"):
         assert G.HashTable(s, 1000, 0.8).stats()["find_staged"] == 0
     # beyond the L2 the other 16-pair schemes find staged too; 32-pair buckets and 1CHT do not
-    for s, b, staged in (("p2bht", 16, 1), ("iht", 16, 1), ("bcht_lb", 16, 1), ("p2bht", 32, 0), ("iht", 32, 0)):
+    for s, b, kpl in (("p2bht", 16, 6), ("iht", 16, 6), ("bcht_lb", 16, 6), ("p2bht", 32, 3), ("iht", 32, 3),
+                      ("bcht", 32, 3)):
         st = G.HashTable(s, (l2 // 8) + (1 << 20), 0.8, bucket_size=b).stats()
-        assert (st["find_staged"], st["tile_lanes"]) == (staged, 4 if staged else 8), (s, b)
+        assert (st["find_staged"], st["tile_lanes"], st["keys_per_lane"]) == (1, 4, kpl), (s, b)
     assert G.HashTable("cuckoo1", (l2 // 8) + (1 << 20), 0.5).stats()["find_staged"] == 0
 
 
