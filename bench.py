@@ -391,6 +391,9 @@ def run_ours(args, world, rank, local):
     keys_per_step = len(LFS) * 3 * n
     value = whole_job_value(keys_per_step, args.steps, world, ms)
     gpu_launches = launches[0]
+    # the device build's kernels, read before the end-to-end leg rebuilds the
+    # tables from host buffers (a different build path)
+    st_dev = tables[LFS[0]].stats()
 
     # end to end through the public API from pinned host buffers
     e2e = None
@@ -460,16 +463,18 @@ def run_ours(args, world, rank, local):
 
     peak, peak_src = peaks()
     kernels = {}
-    st0 = tables[LFS[0]].stats()
+    st0 = st_dev
+    bks = build_kernels(st0)
+    has_fill = "fill_kernel" in bks  # else the placement writes every line: no fill to rate
     find_name = "bcht_find_async_kernel" if st0["find_staged"] else "bucketed_find_kernel"
     for lf in LFS:
         # a build's work after the fill: the grouping and the ranked placement
         # (when the build does them) and the cuckoo insert, timed together
         phase_ms[f"build@{lf}"] = [a + b + c for a, b, c in zip(phase_ms[f"group@{lf}"], phase_ms[f"place@{lf}"],
                                                                phase_ms[f"insert@{lf}"])]
-        for op, key, pp in (("fill", "fill", 0.0), ("insert", "build", probes[lf]["insert"]),
-                            ("find", "find_pos", probes[lf]["find_pos"]),
-                            ("find", "find_neg", probes[lf]["find_neg"])):
+        for op, key, pp in ((("fill", "fill", 0.0),) if has_fill else ()) + (
+                ("insert", "build", probes[lf]["insert"]), ("find", "find_pos", probes[lf]["find_pos"]),
+                ("find", "find_neg", probes[lf]["find_neg"])):
             t_ms = statistics.median(phase_ms[f"{key}@{lf}"])
             bpk = bytes_per_key(op, pp, lf)
             gbs = bpk * n / (t_ms / 1e3) / 1e9
@@ -477,12 +482,11 @@ def run_ours(args, world, rank, local):
                                       "bytes_per_key": round(bpk, 2), "achieved_gbs": round(gbs, 1),
                                       "frac_of_hbm": round(gbs / peak, 4)}
     # dominant kernel = the kernel function with the most device time per step
-    bks = build_kernels(st0)
     build_name = "+".join(dict.fromkeys(k for k in bks if k != "fill_kernel"))
     funcs = {find_name: [k for k in kernels if k.startswith("find")],
-             build_name: [k for k in kernels if k.startswith("build")],
-             # the fill, or the control block's reset when the placement writes every line
-             ("fill_kernel" if "fill_kernel" in bks else "control_reset"): [k for k in kernels if k.startswith("fill")]}
+             build_name: [k for k in kernels if k.startswith("build")]}
+    if has_fill:
+        funcs["fill_kernel"] = [k for k in kernels if k.startswith("fill")]
     per_func = {}
     for f, ks in funcs.items():
         t_ms = sum(kernels[k]["ms"] for k in ks)
