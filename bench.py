@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--keys-per-lane", type=int, default=0, help="find: query sets in flight per lane")
     ap.add_argument("--build-keys-per-lane", type=int, default=0, help="insert: keys in flight per lane")
     ap.add_argument("--find-async", type=int, default=0, choices=[-1, 0, 1])
+    ap.add_argument("--find-grouped", type=int, default=0, choices=[-1, 0, 1],
+                    help="grouped find (rounds by table range, opt-in): 1 on, else per query")
     ap.add_argument("--group-build", type=int, default=0, choices=[-1, 0, 1],
                     help="1: group the pairs by first-choice bucket range before the build")
     ap.add_argument("--ranked-build", type=int, default=0, choices=[-1, 0],
@@ -174,6 +176,16 @@ def build_kernels(st: dict) -> list[str]:
     if st["last_build_ranked"]:
         ks += ["rank_place_kernel"]
     return ks + ["bucketed_insert_kernel"]
+
+
+def find_kernels(st: dict) -> list[str]:
+    """The library kernels one find launches, from the table's stats."""
+    if st["last_find_grouped"]:  # per round: two groupings and the lookup; then the return to query order
+        rnd = ["region_cursors_kernel", "group_scatter_kernel", "region_cursors_kernel", "group_scatter_kernel",
+               "grouped_lookup_kernel"]
+        return rnd * st["num_hashes"] + ["grouped_spill_kernel"] + ["region_cursors_kernel", "group_scatter_kernel"] * 2 \
+            + ["window_write_kernel"]
+    return ["bcht_find_async_kernel" if st["find_staged"] else "bucketed_find_kernel"]
 
 
 def kernel_source_hash() -> str:
@@ -333,6 +345,8 @@ def run_ours(args, world, rank, local):
         cfg["build_keys_per_lane"] = args.build_keys_per_lane
     if args.find_async:
         cfg["find_async"] = args.find_async
+    if args.find_grouped:
+        cfg["find_grouped"] = args.find_grouped
     tables = {lf: G.HashTable("bcht", n, lf, seed=seed, **cfg) for lf in LFS}
     torch.cuda.synchronize()
 
@@ -353,7 +367,7 @@ def run_ours(args, world, rank, local):
             e1.record()
             t.find(neg, out)
             e2.record()
-            launches[0] += 2
+            launches[0] += 2 * len(find_kernels(t.stats()))
             if record:
                 phase_ms[f"fill@{lf}"].append(st["last_fill_ms"])
                 phase_ms[f"group@{lf}"].append(max(st["last_group_ms"], 0.0))
@@ -466,7 +480,7 @@ def run_ours(args, world, rank, local):
     st0 = st_dev
     bks = build_kernels(st0)
     has_fill = "fill_kernel" in bks  # else the placement writes every line: no fill to rate
-    find_name = "bcht_find_async_kernel" if st0["find_staged"] else "bucketed_find_kernel"
+    find_name = "+".join(dict.fromkeys(find_kernels(st0)))
     for lf in LFS:
         # a build's work after the fill: the grouping and the ranked placement
         # (when the build does them) and the cuckoo insert, timed together

@@ -136,6 +136,22 @@ typedef struct {
    * loses a CAS to a slot that stays filled). A smaller value only serves to
    * test that the device loop ends and the error reaches the caller. */
   uint32_t max_steps;
+  /* Grouped find of device queries (16-pair buckets: BCHT, P2BHT, IHT, the
+   * load-balanced BCHT): the same probes with the same stop rule as every
+   * other find (Sec. V), made round by round -- round r reads bucket H_r of
+   * every query still open, the queries grouped by 64 KB range of the table
+   * so each range is read once per round from shared memory -- and the
+   * answers returned to query order by position. 1 = on; 0 or -1 = off
+   * (the default: on GB300 the grouped find is faster for batches of mostly
+   * missing keys -- 2^28 misses against a 2^28-key BCHT at LF 0.99: 16.6 ms
+   * against 19.9 ms -- and slower for mostly present ones, 10.4 against 9.8
+   * ms). Needs scratch (the library pool for tables on library storage, else
+   * ght_set_build_scratch's buffer when large enough; ght_find_scratch_bytes),
+   * 16-byte aligned queries, tables of up to 2^25 buckets and batches of at
+   * least ~5500 queries per group of 2^shift buckets (shift = bits of the
+   * bucket count - 9); where these do not hold, the find runs per query.
+   * Other shapes (32-pair buckets, CUCKOO1, the set) reject 1. */
+  int32_t find_grouped;
 } ght_config;
 
 typedef struct {
@@ -172,6 +188,8 @@ typedef struct {
    * none, as for a build read in place, or not complete) and the bytes copied */
   double last_h2d_ms;
   uint64_t last_h2d_bytes;
+  int32_t find_grouped;        /* the table's grouped-find setting (1 on, else off) */
+  int32_t last_find_grouped;   /* 1 if the last ght_find ran grouped */
 } ght_stats_t;
 
 /* Library version string; never NULL. */
@@ -298,10 +316,17 @@ int ght_unpermute(const uint32_t *d_src, const uint32_t *d_pos, uint64_t n, uint
  * builds without grouping). */
 uint64_t ght_build_scratch_bytes(const ght_table *t, uint64_t n);
 
+/* Device scratch a ght_find of n device queries uses when it runs grouped
+ * (config find_grouped): about 45 bytes per query; 0 if such a find runs per
+ * query and needs none. */
+uint64_t ght_find_scratch_bytes(const ght_table *t, uint64_t n);
+
 /* Caller-owned device scratch (256-byte aligned, `bytes` long, kept alive
- * by the caller) for later builds; NULL clears it. Without it, a table whose
- * storage the library owns takes grouping scratch from the library's
- * stream-ordered pool, and a table on caller storage builds ungrouped. */
+ * by the caller) for later builds and grouped finds; NULL clears it. Without
+ * it (or where it is smaller than the call needs), a table whose storage the
+ * library owns takes scratch from the library's stream-ordered pool, and a
+ * table on caller storage builds ungrouped and finds per query. Calls that
+ * use this buffer must not overlap on the device (they share it). */
 int ght_set_build_scratch(ght_table *t, void *d_scratch, uint64_t bytes);
 
 /* Fill *out (synchronises the stream when probe counters are on). */

@@ -18,7 +18,7 @@ from ._binding import (  # noqa: F401
     ght_build, ght_build_host, ght_create, ght_create_ex, ght_default_config, ght_destroy,
     ght_export, ght_find, ght_find_host, ght_find_host_noalloc, ght_hash_device, ght_hash_host, ght_last_error, ght_probe_lines,
     ght_reset_counters, ght_set_stream, ght_stats, ght_table_bytes, ght_version, lib, lib_path,
-    NOALLOC_MAX_QUERIES, ght_build_scratch_bytes, ght_set_build_scratch,
+    NOALLOC_MAX_QUERIES, ght_build_scratch_bytes, ght_find_scratch_bytes, ght_set_build_scratch,
 )
 
 __all__ = [

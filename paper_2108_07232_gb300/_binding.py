@@ -36,6 +36,7 @@ class GhtConfig(C.Structure):
         ("build_tile_lanes", C.c_int32), ("build_keys_per_lane", C.c_int32),
         ("build_blocks_per_sm", C.c_int32), ("group_build", C.c_int32), ("ranked_build", C.c_int32),
         ("find_async", C.c_int32), ("check_duplicates", C.c_int32), ("max_steps", C.c_uint32),
+        ("find_grouped", C.c_int32),
     ]
 
 
@@ -54,6 +55,7 @@ class GhtStats(C.Structure):
         ("last_build_ranked", C.c_int32), ("last_place_ms", C.c_double), ("place_overflow", C.c_uint64),
         ("find_staged", C.c_int32), ("last_build_split", C.c_int32),
         ("last_h2d_ms", C.c_double), ("last_h2d_bytes", C.c_uint64),
+        ("find_grouped", C.c_int32), ("last_find_grouped", C.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -143,6 +145,7 @@ def lib():
                 "ght_find_host_noalloc": ([vp, vp, vp, u64], i32),
                 "ght_stats": ([vp, C.POINTER(GhtStats)], i32),
                 "ght_build_scratch_bytes": ([vp, u64], u64),
+                "ght_find_scratch_bytes": ([vp, u64], u64),
                 "ght_set_build_scratch": ([vp, vp, u64], i32),
                 "ght_reset_counters": ([vp], i32),
                 "ght_export": ([vp, vp, u64], i32),
@@ -278,6 +281,10 @@ def ght_build_scratch_bytes(t: int, n: int) -> int:
     return int(lib().ght_build_scratch_bytes(t, n))
 
 
+def ght_find_scratch_bytes(t: int, n: int) -> int:
+    return int(lib().ght_find_scratch_bytes(t, n))
+
+
 def ght_set_build_scratch(t: int, d_scratch, nbytes: int) -> None:
     _check(lib().ght_set_build_scratch(t, _ptr(d_scratch), nbytes))
 
@@ -410,8 +417,14 @@ class HashTable:
 
     def _ensure_scratch(self, n: int) -> None:
         """Two-phase and grouped builds need scratch; it is a torch tensor kept with the table."""
+        self._ensure_bytes(ght_build_scratch_bytes(self._t, n))
+
+    def _ensure_find_scratch(self, n: int) -> None:
+        """A grouped find (find_grouped = 1) needs scratch too: the same buffer, grown."""
+        self._ensure_bytes(ght_find_scratch_bytes(self._t, n))
+
+    def _ensure_bytes(self, need: int) -> None:
         import torch
-        need = ght_build_scratch_bytes(self._t, n)
         have = getattr(self, "_scratch_bytes", 0)
         if need and need > have:
             self._scratch = torch.empty(need + 256, dtype=torch.uint8, device=self.device)
@@ -434,6 +447,7 @@ class HashTable:
         with _device_of(self.device):
             self._stream()
             if q.is_cuda:
+                self._ensure_find_scratch(q.numel())
                 ght_find(self._t, q, out, q.numel())
             else:
                 ght_find_host(self._t, q, out, q.numel())

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libght.so")
 SOURCES = ["ght_api.cu", "ght_host.cu", "ght_batch_api.cu", "ght_pool.cu", "kern_bcht.cu", "kern_other.cu", "kern_group.cu",
-           "kern_batch.cu", "kern_set.cu", "kern_probe.cu", "ght_shard.cu", "kern_place.cu"]
+           "kern_batch.cu", "kern_set.cu", "kern_probe.cu", "ght_shard.cu", "kern_place.cu", "kern_gfind.cu"]
 HEADERS = ["ght_bulk.cuh", "ght_device.cuh", "ght_find.cuh", "ght_find_async.cuh", "ght_kernels.cuh", "ght_internal.h", "ght_host.h", "ght_batch.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -43,6 +43,7 @@ struct Shape {
   int check_dups;    // 1: a successful build checks that no key is stored twice
   int slot_bytes;   // 8 (key/value pair) or 4 (keys-only set)
   uint32_t max_steps;  // per-key step bound of the insert kernels (0: derived)
+  int find_grouped;    // 1: grouped find (rounds by bucket range), else per query
   uint64_t m;
 };
 
@@ -110,6 +111,7 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
     d.find_async = user->find_async;
     d.check_duplicates = user->check_duplicates;
     d.max_steps = user->max_steps;
+    d.find_grouped = user->find_grouped;
     if (user->threshold) d.threshold = user->threshold;
     else if (scheme == GHT_IHT) d.threshold = (4 * d.bucket_size + 4) / 5;  // ceil(0.8 b)
   }
@@ -171,6 +173,10 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
     return fail(GHT_ERR_INVALID_ARG, "4-lane find tiles of the set need the staged find");
   if (async_find ? (d.keys_per_lane < 2 || d.keys_per_lane > max_sets) : (d.keys_per_lane != 1 && d.keys_per_lane != 2))
     return fail(GHT_ERR_INVALID_ARG, "keys per lane must be 1 or 2 (2 to %d for the staged find)", max_sets);
+  // the grouped find reads 16-pair buckets (BCHT, P2BHT, IHT, the load-balanced BCHT)
+  const bool grouped_shape = scheme != GHT_CUCKOO1 && scheme != GHT_BCHT_SET && b == 16;
+  if (d.find_grouped > 0 && !grouped_shape)
+    return fail(GHT_ERR_INVALID_ARG, "the grouped find is for tables of 16-pair buckets");
   s->scheme = scheme;
   s->b = b;
   s->h = h;
@@ -191,6 +197,7 @@ int resolve(int scheme, uint64_t capacity, double lf, const ght_config *user, Sh
   s->find_async = async_find ? 1 : 0;
   s->check_dups = d.check_duplicates > 0 ? 1 : 0;
   s->max_steps = d.max_steps;
+  s->find_grouped = grouped_shape ? d.find_grouped : -1;
   s->m = (uint64_t)want;
   return GHT_OK;
 }
@@ -326,6 +333,7 @@ struct ght_table {
   bool last_grouped = false;
   bool last_split = false;
   bool last_ranked = false;
+  mutable bool last_find_grouped = false;
   uint64_t place_overflow = 0;
   void *scratch = nullptr;  // caller-owned build scratch (ght_set_build_scratch)
   uint64_t scratch_bytes = 0;
@@ -516,7 +524,175 @@ cudaError_t launch_place(const ght_table *t, const uint32_t *k, const uint32_t *
   return ght::launch_place_bcht(t->shape.b, t->view(), k, v, n, pb, count, t->stream);
 }
 
+// Grouped find (kern_gfind.cu): shape of the two grouping levels of each
+// round (by H_r bucket range: 2^shift-bucket groups, then 64 KB sub-groups)
+// and of the return to query order (by position: 2^20-position groups, then
+// 2^13-position windows). Regions are sized for the whole batch, which
+// bounds every round's list.
+struct GFindShape {
+  int shift = 0;
+  uint32_t groups = 0, region1 = 0;
+  SubShape sub;
+  uint32_t rgroups = 0, rbins = 0;
+  uint64_t l1_len = 0, l2_len = 0;
+};
+
+constexpr int kRetShift1 = 20;
+
+bool gfind_shape(const ght_table *t, uint64_t n, GFindShape *g) {
+  if (n == 0 || n > 0xFFFFFFFFull - (1ull << kRetShift1)) return false;
+  group_shape(t->shape.m, &g->shift, &g->groups);
+  g->region1 = group_region(n, g->groups);
+  if (!g->region1 || g->region1 < ght::kSubgroupMinRegion) return false;
+  // second level: sub-groups of 2^kGFindFineShift buckets, at most 256 per group
+  g->sub.fine_shift = std::min(g->shift, ght::kGFindFineShift);
+  g->sub.subs_log2 = g->shift - g->sub.fine_shift;
+  if (g->sub.subs_log2 > 8) return false;
+  g->sub.bins = (uint32_t)(((t->shape.m - 1) >> g->sub.fine_shift) + 1);
+  g->sub.region2 = group_region(n, g->sub.bins);
+  if (!g->sub.region2) return false;
+  g->rgroups = (uint32_t)((n + (1ull << kRetShift1) - 1) >> kRetShift1);
+  g->rbins = (uint32_t)((n + (1ull << ght::kGFindWindowLog2) - 1) >> ght::kGFindWindowLog2);
+  g->l1_len = std::max<uint64_t>((uint64_t)g->groups * g->region1, (uint64_t)g->rgroups << kRetShift1);
+  g->l2_len = std::max<uint64_t>((uint64_t)g->sub.bins * g->sub.region2, (uint64_t)g->rbins << ght::kGFindWindowLog2);
+  return g->l2_len <= 0xFFFFFFFFull;
+}
+
+// scratch: [counters][cursors: level 1, level 2, return 1, return 2][level-1
+// keys, positions][level-2 keys, positions, buckets][next-round keys,
+// positions][answers: positions, values][spill: keys, positions, rounds]
+constexpr uint64_t kGFindCounters = 64;  // 8-byte counters
+uint64_t gfind_scratch_bytes(const GFindShape &g, uint64_t n) {
+  const uint64_t cur = 2 * align256(ght::kMaxGroups * 4ull) + 2 * align256(std::max<uint64_t>(g.sub.bins, g.rbins) * 4ull);
+  return kGFindCounters * 8 + cur + 2 * align256(g.l1_len * 4) + 2 * align256(g.l2_len * 4) + align256(g.l2_len) +
+         7 * align256(n * 4);
+}
+
+// Whether a find of n device queries runs grouped: only where config
+// find_grouped is 1. Measured on GB300 with 2^28 queries against a 2^28-key
+// BCHT (2.2 GB of slots): grouped 16.6 / 12.0 ms against 19.9 / 12.8 ms per
+// query for all-missing keys at LF 0.99 / 0.9, but 10.4 / 9.1 against 9.8 /
+// 7.8 ms for all-present keys -- the answers' return to query order (2.6 ms)
+// costs more than the rounds save when most queries end at their first
+// bucket -- so the per-query find stays the default.
+bool wants_grouped_find(const ght_table *t, uint64_t n) { return t->shape.find_grouped > 0 && n > 0; }
+
+// The grouped find's launches on the table's stream. Returns cudaErrorNotSupported
+// (nothing launched) where the batch's shape or scratch does not allow it.
+cudaError_t launch_find_grouped(const ght_table *t, const uint32_t *q, uint32_t *out, uint64_t n) {
+  GFindShape g;
+  if ((reinterpret_cast<uintptr_t>(q) & 15u) || !gfind_shape(t, n, &g)) return cudaErrorNotSupported;
+  const uint64_t need = gfind_scratch_bytes(g, n);
+  void *pool_buf = nullptr;
+  char *scr = nullptr;
+  if (t->scratch && t->scratch_bytes >= need) scr = static_cast<char *>(t->scratch);
+  else if (t->owns_storage && pool_alloc(&pool_buf, need, t->stream) == cudaSuccess) scr = static_cast<char *>(pool_buf);
+  if (!scr) {
+    cudaGetLastError();
+    return cudaErrorNotSupported;
+  }
+  const cudaStream_t s = t->stream;
+  const bool early = t->shape.scheme == GHT_BCHT;
+  const bool count = t->shape.count_probes != 0;
+  char *p = scr;
+  unsigned long long *ctr = reinterpret_cast<unsigned long long *>(p);  // [0..4): claims, [4..8): next-round counts,
+  p += kGFindCounters * 8;                                              // [8]: answers, [9]: spill
+  auto take = [&](uint64_t bytes) {
+    char *r = p;
+    p += align256(bytes);
+    return reinterpret_cast<uint32_t *>(r);
+  };
+  const uint64_t bins_max = std::max<uint64_t>(g.sub.bins, g.rbins);
+  uint32_t *cur1 = take(ght::kMaxGroups * 4ull), *cur_r1 = take(ght::kMaxGroups * 4ull);
+  uint32_t *cur2 = take(bins_max * 4), *cur_r2 = take(bins_max * 4);
+  uint32_t *l1k = take(g.l1_len * 4), *l1p = take(g.l1_len * 4);
+  uint32_t *l2k = take(g.l2_len * 4), *l2p = take(g.l2_len * 4);
+  uint8_t *l2b = reinterpret_cast<uint8_t *>(take(g.l2_len));  // each item's bucket within its sub-group
+  uint32_t *ck = take(n * 4), *cp = take(n * 4);
+  uint32_t *rp = take(n * 4), *rv = take(n * 4);
+  ght::SpillList spill;
+  spill.k = take(n * 4);
+  spill.v = take(n * 4);
+  spill.round = take(n * 4);
+  spill.count = ctr + 9;
+  spill.cap = n;
+  ght::GroupedFindLists fl;
+  fl.res_p = rp;
+  fl.res_v = rv;
+  fl.res_count = ctr + 8;
+  fl.cont_k = ck;
+  fl.cont_p = cp;
+  fl.cap = n;
+  cudaError_t e = cudaMemsetAsync(ctr, 0, kGFindCounters * 8, s);
+  ght::SubSplit ss;
+  ss.ends1 = cur1;
+  ss.region1 = g.region1;
+  ss.region1_M = ght::make_fastmod(g.region1).M;
+  ss.fine_shift = g.sub.fine_shift;
+  ss.subs_log2 = g.sub.subs_log2;
+  ss.groups = g.groups;
+  for (int r = 0; r < t->shape.h && e == cudaSuccess; ++r) {
+    ght::TableView tv = t->view();
+    tv.first = r;  // the groupings of round r go by H_r
+    ght::GroupExtras x;
+    x.spill = spill;
+    if (r == 0) {  // the queries themselves, with their positions
+      e = ght::launch_group(tv, q, nullptr, n, g.shift, g.groups, nullptr, cur1, l1k, l1p, s, g.region1, x);
+    } else {  // the items left by round r - 1
+      x.d_n = ctr + 4 + (r - 1);
+      e = ght::launch_group(tv, ck, cp, n, g.shift, g.groups, nullptr, cur1, l1k, l1p, s, g.region1, x);
+    }
+    if (e == cudaSuccess) {
+      ght::GroupExtras x2;
+      x2.spill = spill;
+      x2.out_b = l2b;
+      e = ght::launch_subgroup(tv, l1k, l1p, (uint64_t)g.groups * g.region1, ss, g.sub.bins, cur2, g.sub.region2, l2k,
+                               l2p, s, x2);
+    }
+    if (e == cudaSuccess) {
+      ght::GroupedFindLists fr = fl;
+      fr.claim = ctr + r;
+      fr.cont_count = ctr + 4 + r;
+      e = ght::launch_grouped_lookup(tv, r, early, count, l2k, l2p, l2b, cur2, g.sub.region2, g.sub.bins,
+                                     g.sub.fine_shift, fr, s);
+    }
+  }
+  if (e == cudaSuccess) e = ght::launch_grouped_spill(t->view(), early, count, spill, fl, n, s);
+  // every query has exactly one answer: back to query order by position
+  if (e == cudaSuccess) {
+    ght::GroupExtras xr;
+    xr.ident = true;
+    xr.d_n = fl.res_count;  // n, unless a grouping fault dropped items (kStatusCorrupt)
+    e = ght::launch_group(t->view(), rp, rv, n, kRetShift1, g.rgroups, nullptr, cur_r1, l1k, l1p, s,
+                          1u << kRetShift1, xr);
+  }
+  if (e == cudaSuccess) {
+    ght::SubSplit sr;
+    sr.ends1 = cur_r1;
+    sr.region1 = 1u << kRetShift1;
+    sr.region1_M = ght::make_fastmod(sr.region1).M;
+    sr.fine_shift = ght::kGFindWindowLog2;
+    sr.subs_log2 = kRetShift1 - ght::kGFindWindowLog2;
+    sr.groups = g.rgroups;
+    ght::GroupExtras xr;
+    xr.ident = true;
+    e = ght::launch_subgroup(t->view(), l1k, l1p, (uint64_t)g.rgroups << kRetShift1, sr, g.rbins, cur_r2,
+                             1u << ght::kGFindWindowLog2, l2k, l2p, s, xr);
+  }
+  if (e == cudaSuccess) e = ght::launch_window_write(l2k, l2p, cur_r2, n, out, s);
+  if (pool_buf) cudaFreeAsync(pool_buf, s);
+  return e;
+}
+
 cudaError_t launch_find(const ght_table *t, const uint32_t *q, uint32_t *out, uint64_t n) {
+  t->last_find_grouped = false;
+  if (wants_grouped_find(t, n)) {
+    const cudaError_t eg = launch_find_grouped(t, q, out, n);
+    if (eg != cudaErrorNotSupported) {
+      t->last_find_grouped = eg == cudaSuccess;
+      return eg;
+    }
+  }
   const ght::TableView tv = t->view();
   if (t->shape.scheme == GHT_BCHT) {
     const ght::LaunchOpts o = t->find_opts();
@@ -1095,6 +1271,15 @@ uint64_t ght_build_scratch_bytes(const ght_table *t, uint64_t n) {
   return build_scratch_need(t, n);
 }
 
+uint64_t ght_find_scratch_bytes(const ght_table *t, uint64_t n) {
+  if (!t) {
+    fail(GHT_ERR_INVALID_ARG, "table is NULL");
+    return 0;
+  }
+  GFindShape g;
+  return wants_grouped_find(t, n) && gfind_shape(t, n, &g) ? gfind_scratch_bytes(g, n) : 0;
+}
+
 int ght_set_build_scratch(ght_table *t, void *d_scratch, uint64_t bytes) {
   if (!t) return fail(GHT_ERR_INVALID_ARG, "table is NULL");
   if (d_scratch && ((uintptr_t)d_scratch & 255u) != 0u) return fail(GHT_ERR_INVALID_ARG, "scratch must be 256-byte aligned");
@@ -1141,6 +1326,8 @@ int ght_stats(const ght_table *t, ght_stats_t *out) {
   out->last_place_ms = -1.0;
   out->place_overflow = t->place_overflow;
   out->find_staged = t->shape.find_async;
+  out->find_grouped = t->shape.find_grouped;
+  out->last_find_grouped = t->last_find_grouped ? 1 : 0;
   if (t->timed_build && cudaEventQuery(t->tev[3]) == cudaSuccess) {
     if (cudaEventElapsedTime(&ms, t->tev[0], t->tev[1]) == cudaSuccess) out->last_fill_ms = ms;
     // between the fill and the cuckoo insert: the grouping and/or the ranked placement

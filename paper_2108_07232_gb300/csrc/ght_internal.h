@@ -174,17 +174,38 @@ struct SubSplit {
   uint32_t region1 = 0;             // the grouped array's region per group
   uint64_t region1_M = 0;           // i / region1 = mulhi(region1_M, i)
   int fine_shift = 0;               // sub-group of a key: H_0(k) >> fine_shift
-  int subs_log2 = 0;                // sub-groups per group, log2 (<= 7)
+  int subs_log2 = 0;                // sub-groups per group, log2 (<= 8)
   uint32_t groups = 0;              // groups of the first level
 };
 
+// Where a grouping in region mode puts an item that does not fit its
+// group's region: with count set (a grouped find), appended to this list as
+// (key, value, hash index tv.first); else kStatusGroupRegion is set.
+struct SpillList {
+  uint32_t *k = nullptr, *v = nullptr, *round = nullptr;
+  unsigned long long *count = nullptr;
+  unsigned long long cap = 0;
+};
+
+// Optional parts of a grouping in region mode. d_n: the input's length is
+// min(n, *d_n), read on the device. ident: items are grouped by key >> shift
+// (the key is a position), not by a hash of the key.
+struct GroupExtras {
+  const unsigned long long *d_n = nullptr;
+  SpillList spill;
+  bool ident = false;
+  // second level of a grouped find (sub-groups of at most 256 buckets): each
+  // item's bucket within its sub-group, written beside it
+  uint8_t *out_b = nullptr;
+};
+
 // Reorder the pairs of a region-grouped array (len entries, groups of
-// 2^subs_log2 <= 128 sub-groups) by sub-group into regions of `region` entries:
+// 2^subs_log2 <= 256 sub-groups) by sub-group into regions of `region` entries:
 // sub-group f's pairs go to [f * region, cursors[f]); bins = sub-groups in
 // all. A sub-group with more pairs than its region sets kStatusGroupRegion.
 cudaError_t launch_subgroup(const TableView &tv, const uint32_t *keys, const uint32_t *values, uint64_t len,
                             const SubSplit &sub, uint32_t bins, uint32_t *cursors, uint32_t region, uint32_t *out_k,
-                            uint32_t *out_v, cudaStream_t s);
+                            uint32_t *out_v, cudaStream_t s, const GroupExtras &x = GroupExtras());
 
 // Smallest first-level region a second-level split accepts (smaller regions
 // would leave its tiles mostly empty). Regions are multiples of 8 entries, so
@@ -206,7 +227,31 @@ cudaError_t launch_block_place(int B, bool key_slots, const TableView &tv, const
 // with more than `region` pairs sets kStatusGroupRegion in tv.ctrl.
 cudaError_t launch_group(const TableView &tv, const uint32_t *keys, const uint32_t *values, uint64_t n,
                          int shift, uint32_t groups, uint32_t *counts, uint32_t *cursors, uint32_t *out_k,
-                         uint32_t *out_v, cudaStream_t s, uint32_t region = 0);
+                         uint32_t *out_v, cudaStream_t s, uint32_t region = 0,
+                         const GroupExtras &x = GroupExtras());
+// kern_gfind.cu: grouped bulk find of 16-pair buckets (see grouped_lookup_kernel).
+// Lists of one round: items answered (query position, value) and items left
+// for the next round (key, query position); `cap` entries each.
+struct GroupedFindLists {
+  uint32_t *res_p = nullptr, *res_v = nullptr;
+  unsigned long long *res_count = nullptr;
+  uint32_t *cont_k = nullptr, *cont_p = nullptr;
+  unsigned long long *cont_count = nullptr;
+  unsigned long long *claim = nullptr;  // sub-group claim cursor of the round, zero at launch
+  unsigned long long cap = 0;
+};
+// Sub-groups of a grouped find: 2^8 buckets (32 KB of 16-pair buckets).
+constexpr int kGFindFineShift = 8;
+// Answers return to query order in windows of 2^13 positions (32 KB).
+constexpr int kGFindWindowLog2 = 13;
+cudaError_t launch_grouped_lookup(const TableView &tv, int round, bool early_exit, bool count, const uint32_t *gk,
+                                  const uint32_t *gp, const uint8_t *gb, const uint32_t *ends, uint32_t region,
+                                  uint32_t bins, int fine_shift, const GroupedFindLists &fl, cudaStream_t s);
+cudaError_t launch_grouped_spill(const TableView &tv, bool early_exit, bool count, const SpillList &spill,
+                                 const GroupedFindLists &fl, uint64_t n_queries, cudaStream_t s);
+cudaError_t launch_window_write(const uint32_t *rp, const uint32_t *rv, const uint32_t *ends, uint64_t n,
+                                uint32_t *out, cudaStream_t s);
+
 // dst[pos[j]] = src[j] for j < n.
 cudaError_t launch_unpermute(const uint32_t *src, const uint32_t *pos, uint64_t n, uint32_t *dst, cudaStream_t s);
 

@@ -13,8 +13,19 @@
 
 namespace ght {
 
-__device__ __forceinline__ uint32_t group_of(const TableView &tv, uint32_t k, int shift) {
-  return k == kEmptyKey ? 0u : (bucket_of(tv.hf, 0, k) >> shift);  // sentinels are flagged by the insert
+// The hash a grouping goes by, h_{tv.first} (0 for builds; a grouped find's
+// round r groups by H_r), as hash index 0 of a family, so the per-item hash
+// takes its constants from registers.
+__device__ __forceinline__ HashFamily grouping_hash(const TableView &tv) {
+  HashFamily hf = tv.hf;
+  hf.a[0] = select4(tv.hf.a, tv.first);
+  hf.c[0] = select4(tv.hf.c, tv.first);
+  return hf;
+}
+
+// Group of key k: its bucket under hf's hash 0, shifted down; sentinels go to group 0.
+__device__ __forceinline__ uint32_t group_of(const HashFamily &hf, uint32_t k, int shift) {
+  return k == kEmptyKey ? 0u : (bucket_of(hf, 0, k) >> shift);  // sentinels are flagged by the insert
 }
 
 // Pass 1: per-group counts (block-local histogram in shared memory). With
@@ -24,6 +35,7 @@ __global__ void __launch_bounds__(256)
 group_count_kernel(TableView tv, const uint32_t *__restrict__ keys, uint64_t n, int shift, uint32_t groups,
                    uint32_t *__restrict__ counts) {
   extern __shared__ uint32_t sh[];
+  const HashFamily hf = grouping_hash(tv);
   for (uint32_t i = threadIdx.x; i < groups; i += blockDim.x) sh[i] = 0u;
   __syncthreads();
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -37,16 +49,16 @@ group_count_kernel(TableView tv, const uint32_t *__restrict__ keys, uint64_t n, 
       const uint4 kb = second ? __ldg(k4 + i + stride) : ka;
       const uint32_t a[4] = {ka.x, ka.y, ka.z, ka.w}, b[4] = {kb.x, kb.y, kb.z, kb.w};
 #pragma unroll
-      for (int j = 0; j < 4; ++j) atomicAdd(&sh[group_of(tv, a[j], shift)], 1u);
+      for (int j = 0; j < 4; ++j) atomicAdd(&sh[group_of(hf, a[j], shift)], 1u);
       if (second) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) atomicAdd(&sh[group_of(tv, b[j], shift)], 1u);
+        for (int j = 0; j < 4; ++j) atomicAdd(&sh[group_of(hf, b[j], shift)], 1u);
       }
     }
     head = n4 * 4;
   }
   for (uint64_t i = head + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-    atomicAdd(&sh[group_of(tv, __ldg(keys + i), shift)], 1u);
+    atomicAdd(&sh[group_of(hf, __ldg(keys + i), shift)], 1u);
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < groups; i += blockDim.x)
     if (sh[i]) atomicAdd(&counts[i], sh[i]);
@@ -116,17 +128,32 @@ size_t group_scatter_smem(uint32_t groups) {
 }
 
 // POS: the values are the items' input positions (values is not read).
+// IDENT: the grouping key is the key itself (k >> shift), not a hash of it:
+// a grouped find returns its answers to query order by grouping (position,
+// answer) items by position.
+// d_n: when set, the number of items is min(n, *d_n), read on the device (a
+// list whose length an earlier kernel wrote).
+// spill.count: when set, an item beyond its group's region is appended to the
+// spill list (key, value, tv.first) instead of setting kStatusGroupRegion.
 // SUB: the input is itself grouped into regions (sub.ends1, sub.region1), and
 // each group is split further into 2^sub.subs_log2 sub-groups of
 // H_0 >> sub.fine_shift. Tiles then follow the regions (tile t of group g
 // starts at g * region1 + t * kGroupTile and ends at most at ends1[g]), so
 // `groups` (= 1 << subs_log2) local bins cover a tile, and bin j of a tile of
 // group g is sub-group (g << subs_log2) + j.
-template <bool POS, bool SUB>
+// LB (with SUB, a grouped find's second level): each item's bucket within
+// its sub-group (< 256) is written to out_b beside it.
+template <bool POS, bool SUB, bool IDENT = false, bool LB = false>
 __global__ void __launch_bounds__(kGroupThreads, 2)
 group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint32_t *__restrict__ values,
                      uint64_t n, int shift, uint32_t groups, uint32_t *__restrict__ cursors,
-                     uint32_t *__restrict__ out_k, uint32_t *__restrict__ out_v, uint32_t region, SubSplit sub) {
+                     uint32_t *__restrict__ out_k, uint32_t *__restrict__ out_v, uint32_t region, SubSplit sub,
+                     const unsigned long long *__restrict__ d_n, SpillList spill, uint8_t *__restrict__ out_b) {
+  static_assert(!LB || (SUB && !IDENT && !POS), "bucket indexes come with a second level by hash");
+  if (d_n) {
+    const unsigned long long dn = *d_n;
+    if (dn < n) n = dn;
+  }
   extern __shared__ uint4 gs_smem[];
   uint32_t *bufs = reinterpret_cast<uint32_t *>(gs_smem);  // [2][keys kGroupTile | values kGroupTile]
   uint16_t *gid = reinterpret_cast<uint16_t *>(bufs + 4 * kGroupTile);  // [kGroupTile] group of each reordered item
@@ -137,13 +164,17 @@ group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint
   __shared__ uint32_t warp_sums[kGroupThreads / 32];
   __shared__ int s_abort;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const HashFamily hf = grouping_hash(tv);
   // SUB: tiles per region; a tile's start and length follow its group's pairs
   const uint32_t tpg = SUB ? (sub.region1 + kGroupTile - 1) / kGroupTile : 0u;
   const uint64_t ntiles = SUB ? (uint64_t)sub.groups * tpg : (n + kGroupTile - 1) / kGroupTile;
   auto tile_span = [&](uint64_t tile, uint64_t *t0, uint32_t *tn) {
     if (SUB) {
       const uint32_t g = (uint32_t)(tile / tpg), t = (uint32_t)(tile % tpg);
-      const uint64_t start = (uint64_t)g * sub.region1 + (uint64_t)t * kGroupTile, end = __ldg(sub.ends1 + g);
+      // a group's cursor passes its region's end when the group overflowed
+      // (the items beyond were not written): read the region at most
+      const uint64_t start = (uint64_t)g * sub.region1 + (uint64_t)t * kGroupTile;
+      const uint64_t end = min((uint64_t)__ldg(sub.ends1 + g), (uint64_t)(g + 1u) * sub.region1);
       *t0 = start;
       *tn = end > start ? (uint32_t)(end - start < (uint64_t)kGroupTile ? end - start : (uint64_t)kGroupTile) : 0u;
     } else {
@@ -192,6 +223,10 @@ group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint
     uint64_t t0;
     uint32_t tn;
     tile_span(tile, &t0, &tn);
+    // an empty tile (a region's tail): nothing read or written; the next
+    // iteration's copy goes to the other buffer, and the barrier above
+    // ordered this tile's counter reset before the next one's
+    if (tn == 0u) continue;
     const uint32_t tbulk = tn & ~3u;  // items that came by the bulk copies
     uint32_t *sk = bufs + 2 * b * kGroupTile, *sv = sk + kGroupTile;
     // SUB: the first sub-group of the tile's group
@@ -203,9 +238,20 @@ group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint
       if (i < tn) {
         k[u] = i < tbulk ? sk[i] : __ldg(keys + t0 + i);
         v[u] = POS ? (uint32_t)(t0 + i) : (i < tbulk ? sv[i] : __ldg(values + t0 + i));
-        const uint32_t g = SUB ? (k[u] == kEmptyKey ? 0u : bucket_of(tv.hf, 0, k[u]) >> sub.fine_shift) - bin0
-                               : group_of(tv, k[u], shift);
-        gr[u] = (g << 16) | atomicAdd(&cnt[g], 1u);  // group < 4096, rank < kGroupTile
+        // (IDENT: positions below the batch size give groups in range; the
+        // clamp keeps any other key inside the tile's counters)
+        uint32_t g, lb = 0u;
+        if constexpr (IDENT) {
+          g = min(SUB ? (k[u] >> sub.fine_shift) - bin0 : k[u] >> shift, groups - 1u);
+        } else if constexpr (SUB) {
+          const uint32_t bk = k[u] == kEmptyKey ? 0u : bucket_of(hf, 0, k[u]);
+          g = (bk >> sub.fine_shift) - bin0;
+          if (LB) lb = bk & ((1u << sub.fine_shift) - 1u);
+        } else {
+          g = group_of(hf, k[u], shift);
+        }
+        // group < 4096 (LB: < 256, bucket in bits 24..31), rank < kGroupTile
+        gr[u] = (lb << 24) | (g << 16) | atomicAdd(&cnt[g], 1u);
       }
     }
     __syncthreads();
@@ -248,11 +294,11 @@ group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint
 #pragma unroll
     for (int u = 0; u < kGroupPerThread; ++u) {
       if ((uint32_t)u * kGroupThreads + tid < tn) {
-        const uint32_t g = gr[u] >> 16;
+        const uint32_t g = LB ? (gr[u] >> 16) & 0xFFu : gr[u] >> 16;
         const uint32_t at = pre[g] + (gr[u] & 0xFFFFu);
         sk[at] = k[u];
         sv[at] = v[u];
-        gid[at] = (uint16_t)g;
+        gid[at] = (uint16_t)(LB ? g | ((gr[u] >> 24) << 8) : g);
       }
     }
     if (per <= 2) {
@@ -261,14 +307,25 @@ group_scatter_kernel(TableView tv, const uint32_t *__restrict__ keys, const uint
     }
     __syncthreads();
     for (uint32_t i = tid; i < tn; i += kGroupThreads) {
-      const uint32_t g = gid[i];
+      const uint32_t gl = gid[i];
+      const uint32_t g = LB ? gl & 0xFFu : gl;
       const uint32_t at = base[g] + (i - pre[g]);
-      if (region && at >= (bin0 + g + 1u) * region) {  // beyond the group's region: the caller regroups exactly
-        atomicOr(&tv.ctrl->status, kStatusGroupRegion);
+      if (region && at >= (bin0 + g + 1u) * region) {  // beyond the group's region
+        if (spill.count) {  // a grouped find answers it separately
+          const unsigned long long at_s = atomicAdd(spill.count, 1ull);
+          if (at_s < spill.cap) {
+            spill.k[at_s] = sk[i];
+            spill.v[at_s] = sv[i];
+            spill.round[at_s] = (uint32_t)tv.first;
+          }
+        } else {  // a build regroups exactly
+          atomicOr(&tv.ctrl->status, kStatusGroupRegion);
+        }
         continue;
       }
       out_k[at] = sk[i];
       out_v[at] = sv[i];
+      if (LB) out_b[at] = (uint8_t)(gl >> 8);
     }
     __syncthreads();
   }
@@ -300,7 +357,7 @@ cudaError_t launch_unpermute(const uint32_t *src, const uint32_t *pos, uint64_t 
 
 cudaError_t launch_group(const TableView &tv, const uint32_t *keys, const uint32_t *values, uint64_t n,
                          int shift, uint32_t groups, uint32_t *counts, uint32_t *cursors, uint32_t *out_k,
-                         uint32_t *out_v, cudaStream_t s, uint32_t region) {
+                         uint32_t *out_v, cudaStream_t s, uint32_t region, const GroupExtras &x) {
   if (groups == 0 || groups > kMaxGroups) return cudaErrorInvalidValue;
   if (region) {
     if ((uint64_t)groups * region > 0xFFFFFFFFull) return cudaErrorInvalidValue;
@@ -311,7 +368,9 @@ cudaError_t launch_group(const TableView &tv, const uint32_t *keys, const uint32
     return cudaMemsetAsync(counts, 0, groups * sizeof(uint32_t), s);
   }
   if (n > 0xFFFFFFFFull) return cudaErrorInvalidValue;
+  if ((x.d_n || x.spill.count || x.ident) && !region) return cudaErrorInvalidValue;  // region mode only
   const bool pos = values == nullptr;  // carry input positions instead of values
+  if (pos && x.ident) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(values)) & 15u) return cudaErrorInvalidValue;
   cudaError_t e;
   int blocks = 0;
@@ -326,18 +385,19 @@ cudaError_t launch_group(const TableView &tv, const uint32_t *keys, const uint32
   }
   const uint64_t tiles = (n + kGroupTile - 1) / kGroupTile;
   const size_t smem = group_scatter_smem(groups);
-  auto kern = pos ? group_scatter_kernel<true, false> : group_scatter_kernel<false, false>;
+  auto kern = pos ? group_scatter_kernel<true, false>
+                  : (x.ident ? group_scatter_kernel<false, false, true> : group_scatter_kernel<false, false>);
   e = grid_for_smem(kern, kGroupThreads, smem, tiles * kGroupThreads, 0, &blocks);
   if (e != cudaSuccess) return e;
   kern<<<blocks, kGroupThreads, smem, s>>>(tv, keys, values, n, shift, groups, cursors, out_k, out_v, region,
-                                           SubSplit());
+                                           SubSplit(), x.d_n, x.spill, nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_subgroup(const TableView &tv, const uint32_t *keys, const uint32_t *values, uint64_t len,
                             const SubSplit &sub, uint32_t bins, uint32_t *cursors, uint32_t region, uint32_t *out_k,
-                            uint32_t *out_v, cudaStream_t s) {
-  if (len > 0xFFFFFFFFull || (uint64_t)bins * region > 0xFFFFFFFFull || sub.subs_log2 > 7 || region == 0 ||
+                            uint32_t *out_v, cudaStream_t s, const GroupExtras &x) {
+  if (len > 0xFFFFFFFFull || (uint64_t)bins * region > 0xFFFFFFFFull || sub.subs_log2 > 8 || region == 0 ||
       sub.region1 < kSubgroupMinRegion || (sub.region1 & 7u) || sub.groups == 0)
     return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(values)) & 15u) return cudaErrorInvalidValue;
@@ -348,10 +408,15 @@ cudaError_t launch_subgroup(const TableView &tv, const uint32_t *keys, const uin
   const uint64_t tiles = (uint64_t)sub.groups * ((sub.region1 + kGroupTile - 1) / kGroupTile);
   const size_t smem = group_scatter_smem(local);
   int blocks = 0;
-  auto kern = group_scatter_kernel<false, true>;
+  if (x.d_n) return cudaErrorInvalidValue;  // the input's extent comes from sub.ends1
+  if (x.out_b && (x.ident || sub.fine_shift > 8 || sub.subs_log2 > 8)) return cudaErrorInvalidValue;
+  auto kern = x.ident   ? group_scatter_kernel<false, true, true>
+              : x.out_b ? group_scatter_kernel<false, true, false, true>
+                        : group_scatter_kernel<false, true>;
   e = grid_for_smem(kern, kGroupThreads, smem, tiles * kGroupThreads, 0, &blocks);
   if (e != cudaSuccess) return e;
-  kern<<<blocks, kGroupThreads, smem, s>>>(tv, keys, values, len, 0, local, cursors, out_k, out_v, region, sub);
+  kern<<<blocks, kGroupThreads, smem, s>>>(tv, keys, values, len, 0, local, cursors, out_k, out_v, region, sub,
+                                           nullptr, x.spill, x.out_b);
   return cudaGetLastError();
 }
 

@@ -80,7 +80,9 @@ block_place_kernel(TableView tv, const uint32_t *__restrict__ pk, const uint32_t
     for (uint32_t i = tid; i < nb * kVecB; i += kBPThreads) bp_img[i] = e;
     for (uint32_t i = tid; i < nb; i += kBPThreads) bcnt[i] = 0u;
     __syncthreads();
-    const uint32_t s0 = f * region, s1 = ends[f];
+    // a sub-group's cursor passes its region's end when it overflowed (the
+    // pairs beyond were not written; the build regroups exactly)
+    const uint32_t s0 = f * region, s1 = min(ends[f], s0 + region);
     for (uint32_t i0 = s0; i0 < s1; i0 += kBPBatch * kBPThreads) {
       uint32_t k[kBPBatch], v[kBPBatch];
 #pragma unroll
