@@ -160,7 +160,7 @@ class ClockSampler:
 # at 2^28 keys. It describes the kernel source it was captured from,
 # identified by a hash of the find kernel's headers; after any change to them
 # the traffic is reported as null.
-FIND_TRAFFIC = {"bytes_per_launch": 60417126976, "source_sha256_16": "1263724a61e3e7c0",
+FIND_TRAFFIC = {"bytes_per_launch": 60417729344, "source_sha256_16": "0d2326c412189cc0",
                "kernel": "bcht_find_async_kernel"}
 
 
@@ -351,7 +351,8 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
 
     launches = [0]
-    phase_ms = {f"{op}@{lf}": [] for lf in LFS for op in ("fill", "group", "place", "insert", "find_pos", "find_neg")}
+    phase_ms = {f"{op}@{lf}": [] for lf in LFS
+                for op in ("fill", "group", "split", "place", "insert", "find_pos", "find_neg")}
 
     def step(record: bool):
         for lf in LFS:
@@ -371,6 +372,7 @@ def run_ours(args, world, rank, local):
             if record:
                 phase_ms[f"fill@{lf}"].append(st["last_fill_ms"])
                 phase_ms[f"group@{lf}"].append(max(st["last_group_ms"], 0.0))
+                phase_ms[f"split@{lf}"].append(max(st["last_split_ms"], 0.0))
                 phase_ms[f"place@{lf}"].append(max(st["last_place_ms"], 0.0))
                 phase_ms[f"insert@{lf}"].append(st["last_insert_ms"])
                 e2.synchronize()
@@ -482,10 +484,12 @@ def run_ours(args, world, rank, local):
     has_fill = "fill_kernel" in bks  # else the placement writes every line: no fill to rate
     find_name = "+".join(dict.fromkeys(find_kernels(st0)))
     for lf in LFS:
-        # a build's work after the fill: the grouping and the ranked placement
-        # (when the build does them) and the cuckoo insert, timed together
-        phase_ms[f"build@{lf}"] = [a + b + c for a, b, c in zip(phase_ms[f"group@{lf}"], phase_ms[f"place@{lf}"],
-                                                               phase_ms[f"insert@{lf}"])]
+        # a build's work after the fill: the grouping (one or two levels) and
+        # the ranked placement (when the build does them) and the cuckoo
+        # insert, timed together
+        phase_ms[f"build@{lf}"] = [a + b + c + d for a, b, c, d in
+                                   zip(phase_ms[f"group@{lf}"], phase_ms[f"split@{lf}"], phase_ms[f"place@{lf}"],
+                                       phase_ms[f"insert@{lf}"])]
         for op, key, pp in ((("fill", "fill", 0.0),) if has_fill else ()) + (
                 ("insert", "build", probes[lf]["insert"]), ("find", "find_pos", probes[lf]["find_pos"]),
                 ("find", "find_neg", probes[lf]["find_neg"])):
@@ -554,7 +558,7 @@ def run_ours(args, world, rank, local):
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clocks,
             "kernels": kernels, "kernel_functions": per_func, "probes_per_key": probes,
             "build_phases_ms": {str(lf): {ph: round(statistics.median(phase_ms[f"{ph}@{lf}"]), 4)
-                                         for ph in ("fill", "group", "place", "insert")} for lf in LFS},
+                                         for ph in ("fill", "group", "split", "place", "insert")} for lf in LFS},
             "pattern_ceilings": ceilings, "served": served, "batched": batched,
         }
         print(json.dumps(line), flush=True)

@@ -190,6 +190,10 @@ typedef struct {
   uint64_t last_h2d_bytes;
   int32_t find_grouped;        /* the table's grouped-find setting (1 on, else off) */
   int32_t last_find_grouped;   /* 1 if the last ght_find ran grouped */
+  /* device time of the last build's second grouping level (the split into
+   * 64 KB sub-groups of a block placement; -1 if none); last_group_ms is
+   * then the first level alone */
+  double last_split_ms;
 } ght_stats_t;
 
 /* Library version string; never NULL. */

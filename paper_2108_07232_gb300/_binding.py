@@ -55,7 +55,7 @@ class GhtStats(C.Structure):
         ("last_build_ranked", C.c_int32), ("last_place_ms", C.c_double), ("place_overflow", C.c_uint64),
         ("find_staged", C.c_int32), ("last_build_split", C.c_int32),
         ("last_h2d_ms", C.c_double), ("last_h2d_bytes", C.c_uint64),
-        ("find_grouped", C.c_int32), ("last_find_grouped", C.c_int32),
+        ("find_grouped", C.c_int32), ("last_find_grouped", C.c_int32), ("last_split_ms", C.c_double),
     ]
 
     def as_dict(self) -> dict:

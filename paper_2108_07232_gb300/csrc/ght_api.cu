@@ -326,7 +326,8 @@ struct ght_table {
   // timing events: fill start, fill end, pre-insert work end (grouping and/or ranked placement),
   // insert end, find start, find end, grouping end (when a grouped build also places by rank),
   // first and last host-to-device copy of the last host-buffer call
-  cudaEvent_t tev[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  // first grouping level end (when a second level splits the groups)
+  cudaEvent_t tev[10] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   mutable bool timed_h2d = false;
   mutable uint64_t h2d_bytes = 0;
   bool timed_build = false;
@@ -791,6 +792,7 @@ int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n,
     if (grouped) {
       e = ght::launch_group(tv, k, v ? v : k, n, shift, groups, counts, cursors, gk, gv, t->stream, region);
       if (e == cudaSuccess && two_level) {
+        cudaEventRecord(t->tev[9], t->stream);
         ght::SubSplit ss;
         ss.ends1 = cursors;
         ss.region1 = region;
@@ -988,7 +990,7 @@ ght_table *ght_create_ex(int scheme, uint64_t capacity, double load_factor, uint
   t->slots = reinterpret_cast<uint64_t *>(reinterpret_cast<char *>(t->storage) + kCtrlBytes);
   cudaError_t e = cudaMallocHost(reinterpret_cast<void **>(&t->h_ctrl), kCtrlBytes);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->done, cudaEventDisableTiming);
-  for (int i = 0; i < 9 && e == cudaSuccess; ++i) e = cudaEventCreate(&t->tev[i]);
+  for (int i = 0; i < 10 && e == cudaSuccess; ++i) e = cudaEventCreate(&t->tev[i]);
   if (e != cudaSuccess) {
     cuda_fail(e, "creating table resources");
     ght_destroy(t);
@@ -1324,6 +1326,7 @@ int ght_stats(const ght_table *t, ght_stats_t *out) {
   out->slot_bytes = t->shape.slot_bytes;
   out->last_build_ranked = t->last_ranked ? 1 : 0;
   out->last_place_ms = -1.0;
+  out->last_split_ms = -1.0;
   out->place_overflow = t->place_overflow;
   out->find_staged = t->shape.find_async;
   out->find_grouped = t->shape.find_grouped;
@@ -1332,7 +1335,12 @@ int ght_stats(const ght_table *t, ght_stats_t *out) {
     if (cudaEventElapsedTime(&ms, t->tev[0], t->tev[1]) == cudaSuccess) out->last_fill_ms = ms;
     // between the fill and the cuckoo insert: the grouping and/or the ranked placement
     if (t->last_grouped && t->last_ranked) {
-      if (cudaEventElapsedTime(&ms, t->tev[1], t->tev[6]) == cudaSuccess) out->last_group_ms = ms;
+      if (t->last_split) {  // first level, then the second level's split
+        if (cudaEventElapsedTime(&ms, t->tev[1], t->tev[9]) == cudaSuccess) out->last_group_ms = ms;
+        if (cudaEventElapsedTime(&ms, t->tev[9], t->tev[6]) == cudaSuccess) out->last_split_ms = ms;
+      } else if (cudaEventElapsedTime(&ms, t->tev[1], t->tev[6]) == cudaSuccess) {
+        out->last_group_ms = ms;
+      }
       if (cudaEventElapsedTime(&ms, t->tev[6], t->tev[2]) == cudaSuccess) out->last_place_ms = ms;
     } else if (cudaEventElapsedTime(&ms, t->tev[1], t->tev[2]) == cudaSuccess) {
       if (t->last_ranked) out->last_place_ms = ms;

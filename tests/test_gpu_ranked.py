@@ -65,6 +65,8 @@ def test_two_phase_and_cuckoo_only_builds(G, b, lf, group, ranked):
     if want_ranked:
         assert st["last_place_ms"] >= 0.0
         assert (st["last_group_ms"] >= 0.0) == (group > 0)
+        # the second grouping level is timed by itself where it ran
+        assert (st["last_split_ms"] >= 0.0) == bool(st["last_build_split"])
         # keys beyond b arrivals at their first-choice bucket: a few per cent
         # at these load factors (about 9.5 % at 0.99 with b = 16)
         assert 0 < st["place_overflow"] < 0.15 * n
