@@ -160,7 +160,7 @@ class ClockSampler:
 # at 2^28 keys. It describes the kernel source it was captured from,
 # identified by a hash of the find kernel's headers; after any change to them
 # the traffic is reported as null.
-FIND_TRAFFIC = {"bytes_per_launch": 60417729344, "source_sha256_16": "0d2326c412189cc0",
+FIND_TRAFFIC = {"bytes_per_launch": 60460572544, "source_sha256_16": "d0a797b09e952b68",
                "kernel": "bcht_find_async_kernel"}
 
 

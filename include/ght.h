@@ -115,8 +115,9 @@ typedef struct {
   /* Finds of 128-byte buckets (16 pairs: BCHT with 4-lane tiles, P2BHT, IHT
    * and the load-balanced BCHT, whose find tiles then have 4 lanes; the
    * keys-only set, likewise): 1 = stage the bucket parts in shared memory
-   * with asynchronous copies, keys_per_lane (2..8, default 6) query sets in
-   * flight per lane, each scheme's own probe order and stop rule; -1 = off
+   * with asynchronous copies, keys_per_lane (2..8, default 6, of which two
+   * stay in registers) query sets in flight per lane, each scheme's own
+   * probe order and stop rule; -1 = off
    * (bucket parts in registers, keys_per_lane 1..2); 0 = default: on where
    * it applies, the table's slots take at least the device's L2 size and
    * neither keys_per_lane 1 nor (except for BCHT's 4) tile_lanes is given.
