@@ -453,7 +453,8 @@ def run_ours(args, world, rank, local):
                "h2d_bytes_per_step": len(LFS) * (8 * n + 8 * n),
                "d2h_bytes_per_step": len(LFS) * 8 * n,
                "api": "HashTable.build/find on pinned CPU tensors (ght_build_host: the insert reads the pinned "
-                      "pairs in place; ght_find_host: pipelined copies)",
+                      "pairs in place; ght_find_host: the find reads the pinned queries in place, results "
+                      "copied back in pipelined chunks)",
                "step_ms": step_ms,
                "call_ms": {k: round(statistics.median(v), 3) for k, v in call_ms.items()},
                "call_ms_max": {k: round(max(v), 3) for k, v in call_ms.items()},

@@ -308,6 +308,32 @@ def test_build_in_place_from_pinned_host_memory(G, scheme, lf):
         assert (O._u32(t.find(q.cuda()).cpu()) == want).all(), (src, extra)
 
 
+@pytest.mark.parametrize("scheme,lf,nq", [("bcht", 0.99, (1 << 23) + 1001), ("p2bht", 0.8, 1 << 18),
+                                          ("iht", 0.86, 1 << 18), ("cuckoo1", 0.5, 1 << 18),
+                                          ("bcht_set", 0.99, 1 << 18), ("bcht_lb", 0.95, 1 << 18)])
+def test_find_in_place_from_pinned_host_memory(G, scheme, lf, nq):
+    """Page-locked host queries are read in place by the find kernels (no
+    host-to-device copies: last_h2d_ms is -1), pageable ones are staged by
+    copies; both answer as the definitional lookup does, over one chunk of
+    the host pipeline and over two (2^23 + 1001 queries)."""
+    n = (1 << 19) + 77
+    keys, vals = W.make_keys(n, 71), W.make_values(n, 71)
+    sets = scheme == "bcht_set"
+    t = G.HashTable(scheme, n, lf, seed=72)
+    t.build(keys.cuda(), None if sets else vals.cuda())
+    q = W.make_queries(keys, nq, 0.6, seed=73)
+    want = O.lookup(keys, vals, q)
+    if sets:
+        want = (want != O.EMPTY).astype(np.uint32)
+    for src in ("pinned", "pageable"):
+        qq = q.pin_memory() if src == "pinned" else q.clone()
+        got = t.find(qq)
+        assert got.device.type == "cpu"
+        assert (O._u32(got) == want).all(), src
+        copied = t.stats()["last_h2d_ms"] > 0
+        assert copied == (src == "pageable"), src
+
+
 def test_find_follows_the_current_stream(G):
     n = 30000
     t, keys, vals = build_table(G, O.BCHT, n, 0.9)
