@@ -265,8 +265,9 @@ int ght_find_host(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out
  *
  * The queries are copied into a staging array that is part of the library
  * image (a static device array of 2 x GHT_NOALLOC_MAX_QUERIES uint32, 32 MiB),
- * found there by the ordinary find kernel, and the results are copied back
- * into h_out before the call returns. n must not exceed
+ * found there by the ordinary per-query find kernel (also on a table set for
+ * the grouped find, whose scratch would need an allocator), and the results
+ * are copied back into h_out before the call returns. n must not exceed
  * GHT_NOALLOC_MAX_QUERIES (else GHT_ERR_CAPACITY, nothing is done); n = 0 is
  * a no-op. The table must have been built, and the device current at its
  * creation must be current (else GHT_ERR_INVALID_ARG, nothing is done).

@@ -685,9 +685,12 @@ cudaError_t launch_find_grouped(const ght_table *t, const uint32_t *q, uint32_t 
   return e;
 }
 
-cudaError_t launch_find(const ght_table *t, const uint32_t *q, uint32_t *out, uint64_t n) {
+// allow_grouped = false: the per-query find even where the table asks for
+// the grouped one (whose scratch comes from an allocator).
+cudaError_t launch_find(const ght_table *t, const uint32_t *q, uint32_t *out, uint64_t n,
+                        bool allow_grouped = true) {
   t->last_find_grouped = false;
-  if (wants_grouped_find(t, n)) {
+  if (allow_grouped && wants_grouped_find(t, n)) {
     const cudaError_t eg = launch_find_grouped(t, q, out, n);
     if (eg != cudaErrorNotSupported) {
       t->last_find_grouped = eg == cudaSuccess;
@@ -1475,7 +1478,7 @@ extern "C" int ght_find_host_noalloc(const ght_table *t, const uint32_t *h_queri
   uint32_t *d_q = base, *d_o = base + GHT_NOALLOC_MAX_QUERIES;
   e = cudaMemcpyAsync(d_q, h_queries, n * sizeof(uint32_t), cudaMemcpyHostToDevice, t->stream);
   if (e != cudaSuccess) return cuda_fail(e, "copying queries to the staging array");
-  e = launch_find(t, d_q, d_o, n);
+  e = launch_find(t, d_q, d_o, n, false);  // the per-query find: no scratch
   if (e != cudaSuccess) return cuda_fail(e, "launching find");
   e = cudaMemcpyAsync(h_out, d_o, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, t->stream);
   if (e != cudaSuccess) return cuda_fail(e, "copying results back");

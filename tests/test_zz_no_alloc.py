@@ -59,14 +59,17 @@ def test_no_alloc_find_matches_the_allocating_host_find(G):
         assert np.array_equal(out_na, O.lookup(keys, vals, q)), call
 
 
-def test_no_alloc_find_allocates_nothing_on_the_device(G):
+@pytest.mark.parametrize("cfg", [{}, {"find_grouped": 1}])
+def test_no_alloc_find_allocates_nothing_on_the_device(G, cfg):
     """After a first call (and the table's creation, which reserves the
     staging array), further calls leave the device's free memory unchanged:
-    nothing is allocated from the driver, torch or the library's pool."""
+    nothing is allocated from the driver, torch or the library's pool. On a
+    table set for the grouped find, whose scratch would come from an
+    allocator, this entry point still finds per query."""
     lib = G.lib()
     n = 1 << 18
     keys, vals = W.make_keys(n, 79), W.make_values(n, 79)
-    t = G.HashTable("bcht", n, 0.9, seed=6)
+    t = G.HashTable("bcht", n, 0.9, seed=6, **cfg)
     t.build(keys.cuda(), vals.cuda())
     q = W.make_queries(keys, 1 << 21, 0.5, 3).numpy().view(np.uint32).copy()
     rc, _ = _raw_find(lib, "ght_find_host_noalloc", t._t, q)
@@ -81,6 +84,7 @@ def test_no_alloc_find_allocates_nothing_on_the_device(G):
     assert torch.cuda.mem_get_info()[0] == free_before
     assert torch.cuda.memory_reserved() == reserved_before
     assert np.array_equal(out, O.lookup(keys, vals, q))
+    assert t.stats()["last_find_grouped"] == 0
 
 
 def test_no_alloc_find_rejects_batches_beyond_the_staging_array(G):
