@@ -60,16 +60,28 @@ def test_pool_results_same_alone_and_in_the_mix(G, tables):
         out = torch.full_like(q, 7)
         pool.wait(pool.submit_find(ids[t][1], q, out))
         alone.append(out)
+    # in the mix: all submitted at once, waited on afterwards. Requests that
+    # arrive while the pool's launches are busy are packed together; a queue
+    # of large finds submitted first keeps them busy for tens of ms, longer
+    # than the submissions take, so the mix does not depend on how fast this
+    # host submits against how fast the GPU answers.
+    big_t = len(tables) - 1
+    big_q = W.make_queries(tables[big_t][1].cpu(), 1 << 22, 0.5, seed=77).cuda()
+    big_out = torch.empty_like(big_q)
+    blockers = [pool.submit_find(ids[big_t][1], big_q, big_out) for _ in range(300)]
     launches_before = pool.stats()["find_launches"]
-    # in the mix: all submitted at once, waited on afterwards
     mixed, tickets = [], []
     for t, q in reqs:
         out = torch.full_like(q, 9)
         tickets.append(pool.submit_find(ids[t][1], q, out))
         mixed.append(out)
     packed = [pool.wait(tk)["launch_requests"] for tk in tickets]
+    for tk in blockers:
+        assert pool.wait(tk)["status"] == 0
     st = pool.stats()
-    assert st["find_launches"] - launches_before < len(reqs)  # requests were packed together
+    # the blockers take one launch each (each is a full launch's worth of
+    # queries); the 300 mixed requests far fewer than one each
+    assert st["find_launches"] - launches_before < len(reqs) // 2 + len(blockers)
     assert max(packed) > 1
     for (t, q), a, m in zip(reqs, alone, mixed):
         assert torch.equal(a, m)
