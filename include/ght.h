@@ -438,9 +438,11 @@ int ght_batch_run(ght_batch *b, const uint32_t *d_keys, const uint32_t *d_values
                   uint32_t *d_out);
 
 /* Choose the insert and find launch shapes by timing each candidate on
- * these arrays: first the tile shape (lanes per bucket tile, keys per lane),
- * then the grid (1-4 resident blocks per SM, or as many as fit) of the best
- * shape; keeps the fastest. The tables are rebuilt as a side effect. */
+ * these arrays: first the tile shape (lanes per bucket tile, keys per lane;
+ * for finds also 4-lane tiles with 6 query sets per lane, the staged find
+ * whose bucket parts wait in shared memory), then the grid (1-4 resident
+ * blocks per SM, or as many as fit) of the best shape; keeps the fastest.
+ * The tables are rebuilt as a side effect. */
 int ght_batch_autotune(ght_batch *b, const uint32_t *d_keys, const uint32_t *d_values,
                        const uint32_t *d_queries, uint32_t *d_out);
 

@@ -27,6 +27,9 @@ struct BatchView {
 };
 
 bool batch_shape_supported(int tile_lanes, int keys_per_lane);
+// Find shapes: the above, and 4-lane tiles with 6 query sets per lane (the
+// staged find: bucket parts in shared memory).
+bool batch_find_shape_supported(int tile_lanes, int keys_per_lane);
 
 // Describe a built single BCHT table (b = 16) as a batch descriptor (ght_api.cu).
 // Returns false if the table is not a built 16-pair BCHT table.

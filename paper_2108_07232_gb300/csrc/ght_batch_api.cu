@@ -204,7 +204,7 @@ ght_batch *ght_batch_create(uint32_t num_tables, const uint64_t *h_capacities, c
     b->build_o.blocks_per_sm = cfg->build_blocks_per_sm;
     b->find_o.count = b->build_o.count = cfg->count_probes != 0;
   }
-  if (!ght::batch_shape_supported(b->find_o.tile_lanes, b->find_o.keys_per_lane) ||
+  if (!ght::batch_find_shape_supported(b->find_o.tile_lanes, b->find_o.keys_per_lane) ||
       !ght::batch_shape_supported(b->build_o.tile_lanes, b->build_o.keys_per_lane)) {
     fail(GHT_ERR_INVALID_ARG, "unsupported launch shape");
     delete b;
@@ -396,7 +396,7 @@ int ght_batch_autotune(ght_batch *b, const uint32_t *d_keys, const uint32_t *d_v
   // tile shapes (lanes per bucket, keys per lane), then the grid (resident
   // blocks per SM; 0 = as many as fit) of the chosen shape
   static const int kBuild[][2] = {{16, 1}, {8, 1}, {8, 2}, {4, 2}};
-  static const int kFind[][2] = {{4, 2}, {4, 1}, {8, 2}, {8, 1}, {16, 1}};
+  static const int kFind[][2] = {{4, 2}, {4, 1}, {8, 2}, {8, 1}, {16, 1}, {4, 6}};  // {4, 6}: the staged find
   static const int kGrid[] = {0, 1, 2, 3, 4};
   if (b->build_o.blocks_per_sm < 0 || b->find_o.blocks_per_sm < 0) return fail(GHT_ERR_INVALID_ARG, "negative grid");
   auto time_between = [&](float *out_ms) -> int {

@@ -375,7 +375,7 @@ ght_pool *ght_pool_create(uint64_t hbm_budget_bytes, const ght_config *cfg) {
   }
   p->find_o.tile_lanes = p->cfg.tile_lanes;
   p->find_o.keys_per_lane = p->cfg.keys_per_lane;
-  if (!ght::batch_shape_supported(p->find_o.tile_lanes, p->find_o.keys_per_lane)) {
+  if (!ght::batch_find_shape_supported(p->find_o.tile_lanes, p->find_o.keys_per_lane)) {
     fail(GHT_ERR_INVALID_ARG, "unsupported find shape");
     delete p;
     return nullptr;

@@ -8,6 +8,7 @@
 // lane finds the table of the item it takes from a per-chunk hint (one
 // uniform binary search per 32 items) and reads that table's descriptor.
 #include "ght_batch.h"
+#include "ght_find_async.cuh"
 #include "ght_kernels.cuh"
 
 namespace ght {
@@ -454,6 +455,173 @@ batch_find_kernel(BatchView bv, const uint32_t *__restrict__ queries, uint32_t *
 }
 
 // ----------------------------------------------------------------------------
+// The same find with the bucket parts staged in shared memory (the staged
+// find of the single-table path, ght_find_async.cuh): 4-lane tiles, KPL
+// query sets per lane in flight, each set's buckets copied by cp.async (two
+// 16-byte chunks per lane and tile member, chunk positions swizzled by tile)
+// and evaluated KPL - 1 steps after its copies were issued. A query's table
+// comes with it from the batch queue; its bucket address from the table's
+// descriptor. The tables of a batch are each small but are queried all at
+// once, so together their slots exceed the L2 and the reads go to DRAM,
+// where the deeper pipeline pays.
+template <int KPL, int WARPS, bool COUNT>
+__global__ void __launch_bounds__(32 * WARPS)
+batch_find_async_kernel(BatchView bv, const uint32_t *__restrict__ queries, uint32_t *__restrict__ out,
+                        uint64_t per_warp) {
+  constexpr int G = 4;
+  constexpr int kChunks = 8;  // 16-byte chunks per 16-pair bucket
+  extern __shared__ uint4 bfa_smem[];
+  const uint64_t *offs = bv.query_offs;
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int r = lane & (G - 1);
+  const int tbase = lane - r;
+  const unsigned swz = (unsigned)(lane >> 2) & 7u;
+  const unsigned tmask = ((1u << G) - 1u) << tbase;
+  uint4 *wbuf = bfa_smem + (size_t)wib * KPL * 32 * kChunks;
+  const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t lo = __ldg(offs + bv.t_lo), hi = __ldg(offs + bv.t_hi);
+  const uint64_t beg = lo + (gtid >> 5) * per_warp;
+  if (beg >= hi) return;  // whole warp
+  const uint64_t end = beg + per_warp < hi ? beg + per_warp : hi;
+  const unsigned below = lanemask_lt();
+
+  BatchQueue q;
+  bq_init<false>(q, queries, nullptr, beg, end, bv, offs, lane);
+  bool active[KPL];
+  uint32_t key[KPL], act[KPL], tab[KPL];
+  uint64_t idx[KPL];
+  int probe[KPL];
+#pragma unroll
+  for (int s = 0; s < KPL; ++s) {
+    active[s] = false;
+    key[s] = kEmptyKey;
+    act[s] = tab[s] = 0u;
+    idx[s] = 0;
+    probe[s] = 0;
+  }
+  unsigned long long probes = 0, answered = 0;
+
+  for (;;) {
+#pragma unroll
+    for (int s = 0; s < KPL; ++s) {
+      // -- refill set s from the stream, then issue the copies of its buckets
+      const unsigned need = __ballot_sync(kFull, !active[s]);
+      if (need != 0u && q.base + q.head < end) {
+        uint32_t k, unused, tb;
+        const uint64_t at = bq_take<false>(q, queries, nullptr, end, bv, offs, need, below, lane, k, unused, tb);
+        if (at != ~0ull) {
+          if (COUNT) answered++;
+          if (k == kEmptyKey) {
+            out[at] = kEmptyKey;  // the sentinel is never a key
+          } else {
+            active[s] = true;
+            key[s] = k;
+            idx[s] = at;
+            tab[s] = tb;
+            probe[s] = 0;
+          }
+        }
+      }
+      act[s] = __ballot_sync(kFull, active[s]);
+      if (act[s] != 0u) {
+        const uint4 *myb = nullptr;
+        if (active[s]) {
+          const BatchTable &d = bv.tables[tab[s]];
+          myb = reinterpret_cast<const uint4 *>(d.slots) + (uint64_t)batch_bucket(d, probe[s], key[s]) * kChunks;
+        }
+        uint4 *sbuf = wbuf + (size_t)s * 32 * kChunks;
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+          const int owner = tbase + j;
+          const uint4 *src =
+              reinterpret_cast<const uint4 *>(__shfl_sync(kFull, reinterpret_cast<uintptr_t>(myb), owner));
+          if ((act[s] >> owner) & 1u) {
+            uint4 *row = sbuf + owner * kChunks;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+              const unsigned c = 2u * (unsigned)r + (unsigned)i;
+              cp_async16(row + (c ^ swz), src + c);
+            }
+          }
+        }
+      }
+      cp_async_commit();  // one group per set step, empty or not
+      // -- evaluate the set issued KPL - 1 steps ago
+      const int e = (s + 1) % KPL;
+      cp_async_wait<KPL - 1>();
+      __syncwarp();
+      if (act[e] != 0u) {
+        const uint4 *ebuf = wbuf + (size_t)e * 32 * kChunks;
+        bool my_hit = false, my_emp = false;
+        uint32_t my_val = kEmptyKey;
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+          const int owner = tbase + j;
+          const uint32_t kj = __shfl_sync(kFull, key[e], owner);
+          bool hit = false, emp = false;
+          uint32_t hv = 0u;
+          if ((act[e] >> owner) & 1u) {
+            const uint4 *row = ebuf + owner * kChunks;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+              const uint4 c = row[(2u * (unsigned)r + (unsigned)i) ^ swz];  // pairs (c.x, c.y), (c.z, c.w)
+              if (c.x == kj) {
+                hit = true;
+                hv = c.y;
+              }
+              if (c.z == kj) {
+                hit = true;
+                hv = c.w;
+              }
+              emp |= c.x == kEmptyKey || c.z == kEmptyKey;
+            }
+          }
+          const unsigned hb = __ballot_sync(kFull, hit) & tmask;
+          const unsigned eb = __ballot_sync(kFull, emp) & tmask;
+          const uint32_t val = __shfl_sync(kFull, hv, hb ? __ffs(hb) - 1 : lane);
+          if (lane == owner) {
+            my_hit = hb != 0u;
+            my_emp = eb != 0u;
+            my_val = val;
+          }
+        }
+        if ((act[e] >> lane) & 1u) {
+          if (COUNT) probes++;
+          bool finish = false;
+          uint32_t result = kEmptyKey;
+          if (my_hit) {
+            result = my_val;
+            finish = true;
+          } else if (my_emp || ++probe[e] >= bv.h) {  // BCHT: early exit at a bucket with an empty slot
+            finish = true;
+          }
+          if (finish) {
+            out[idx[e]] = result;
+            active[e] = false;
+          }
+        }
+        act[e] = 0u;
+      }
+      __syncwarp();  // set e's buffer is read before the next step reuses it
+    }
+    bool any = false;
+#pragma unroll
+    for (int s = 0; s < KPL; ++s) any |= active[s];
+    if (__ballot_sync(kFull, any) == 0u && q.base + q.head >= end) break;
+  }
+  cp_async_wait<0>();
+  if (COUNT) {
+    probes = warp_sum(probes);
+    answered = warp_sum(answered);
+    if (lane == 0) {
+      atomicAdd(&bv.ctrl->find_probes, probes);
+      atomicAdd(&bv.ctrl->find_queries, answered);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
 template <typename K>
 static cudaError_t launch_sliced(K kern, uint64_t items, int blocks_per_sm, cudaStream_t s, int *blocks,
                                  uint64_t *per_warp) {
@@ -549,6 +717,22 @@ bool batch_shape_supported(int G, int kpl) {
   return (G == 4 || G == 8 || G == 16) && (kpl == 1 || kpl == 2);
 }
 
+bool batch_find_shape_supported(int G, int kpl) { return batch_shape_supported(G, kpl) || (G == 4 && kpl == 6); }
+
+// staged find: 6 query sets per lane, 2-warp blocks (24 KB of shared memory per warp)
+static cudaError_t find_staged(const BatchView &bv, const uint32_t *q, uint32_t *out, uint64_t items,
+                               const LaunchOpts &o, cudaStream_t s) {
+  constexpr int kKpl = 6, kWarps = 2;
+  auto kern = o.count ? batch_find_async_kernel<kKpl, kWarps, true> : batch_find_async_kernel<kKpl, kWarps, false>;
+  const size_t smem = kWarps * find_async_smem_per_warp<kKpl>();
+  int blocks = 0;
+  cudaError_t e = grid_for_smem(kern, 32 * kWarps, smem, items, o.blocks_per_sm, &blocks);
+  if (e != cudaSuccess) return e;
+  const uint64_t warps = (uint64_t)blocks * kWarps;
+  kern<<<blocks, 32 * kWarps, smem, s>>>(bv, q, out, (items + warps - 1) / warps);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_batch_insert(const BatchView &bv, const uint32_t *k, const uint32_t *v, uint64_t items,
                                 const LaunchOpts &o, cudaStream_t s) {
   if (items == 0) return cudaSuccess;
@@ -565,6 +749,7 @@ cudaError_t launch_batch_find(const BatchView &bv, const uint32_t *q, uint32_t *
   const int g = o.tile_lanes, kpl = o.keys_per_lane;
   if (g == 16) return kpl == 1 ? find_cfg<16, 1>(bv, q, out, items, o, s) : find_cfg<16, 2>(bv, q, out, items, o, s);
   if (g == 8) return kpl == 1 ? find_cfg<8, 1>(bv, q, out, items, o, s) : find_cfg<8, 2>(bv, q, out, items, o, s);
+  if (g == 4 && kpl == 6) return find_staged(bv, q, out, items, o, s);
   if (g == 4) return kpl == 1 ? find_cfg<4, 1>(bv, q, out, items, o, s) : find_cfg<4, 2>(bv, q, out, items, o, s);
   return cudaErrorInvalidValue;
 }

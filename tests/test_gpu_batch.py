@@ -85,6 +85,36 @@ def test_batch_plain_and_autotuned_paths_agree(G, work):
         _check_tables(G, c, work, c.run(k, v, q), validate=False)
 
 
+def test_batch_staged_find_parity(G, work):
+    """The staged batch find (4-lane tiles, 6 query sets per lane, bucket
+    parts in shared memory) answers every table's queries as the definitional
+    lookup does, through the graph run and the plain find, on the same
+    tables as the register find; sentinel queries and a table without
+    queries included."""
+    k, v, q = work["keys"].cuda(), work["values"].cuda(), work["queries"].cuda()
+    b = G.Batch(work["capacities"], work["load_factors"], seed=6, tile_lanes=4, keys_per_lane=6)
+    b.set_layout(work["key_offsets"], work["query_offsets"])
+    assert (b.stats()["tile_lanes"], b.stats()["keys_per_lane"]) == (4, 6)
+    out = b.run(k, v, q)
+    _check_tables(G, b, work, out)
+    r = G.Batch(work["capacities"], work["load_factors"], seed=6)
+    r.set_layout(work["key_offsets"], work["query_offsets"])
+    assert torch.equal(r.run(k, v, q), out)
+    # sentinel queries and a table with no queries
+    caps = np.array([0, 5, 100, 3000], dtype=np.uint64)
+    lfs = np.array([0.5, 0.9, 0.95, 0.99])
+    keys, vals = W.make_keys(3105, 19), W.make_values(3105, 19)
+    ko = np.array([0, 0, 5, 105, 3105], dtype=np.uint64)
+    qq = torch.cat([keys[:50], torch.full((7,), -1, dtype=torch.int32), W.make_negatives(3105, 23, 19)])
+    qo = np.array([0, 10, 10, 40, 80], dtype=np.uint64)
+    c = G.Batch(caps, lfs, seed=2, tile_lanes=4, keys_per_lane=6)
+    c.set_layout(ko, qo)
+    got = O._u32(c.run(keys.cuda(), vals.cuda(), qq.cuda()).cpu())
+    for t in range(4):
+        assert (got[qo[t]:qo[t + 1]] == O.lookup(keys[ko[t]:ko[t + 1]], vals[ko[t]:ko[t + 1]],
+                                                  qq[qo[t]:qo[t + 1]])).all(), t
+
+
 def test_batch_edge_cases(G):
     caps = np.array([0, 5, 100, 3000], dtype=np.uint64)
     lfs = np.array([0.5, 0.9, 0.95, 0.99])
