@@ -526,10 +526,10 @@ cudaError_t launch_place(const ght_table *t, const uint32_t *k, const uint32_t *
 }
 
 // Grouped find (kern_gfind.cu): shape of the two grouping levels of each
-// round (by H_r bucket range: 2^shift-bucket groups, then 64 KB sub-groups)
-// and of the return to query order (by position: 2^20-position groups, then
-// 2^13-position windows). Regions are sized for the whole batch, which
-// bounds every round's list.
+// round (by H_r bucket range: 2^shift-bucket groups, then 256-bucket (32 KB)
+// sub-groups) and of the return to query order (by position: 2^20-position
+// groups, then 2^13-position windows). Regions are sized for the whole
+// batch, which bounds every round's list.
 struct GFindShape {
   int shift = 0;
   uint32_t groups = 0, region1 = 0;
