@@ -247,9 +247,7 @@ int ght_find(const ght_table *t, const uint32_t *d_queries, uint32_t *d_out, uin
  * runtime) that requests neither grouping nor the two-phase build
  * (group_build and ranked_build <= 0, the host-buffer defaults) copies
  * nothing: its input-order insert reads them in place (last_h2d_ms -1); they
- * must stay unchanged until the call returns. Likewise a find reads
- * page-locked queries in place (its kernels read them over the host link;
- * only the results are copied back; last_h2d_ms -1). If the bounded wait for the
+ * must stay unchanged until the call returns. If the bounded wait for the
  * device runs out (GHT_ERR_DEVICE_TIMEOUT, see GHT_WAIT_TIMEOUT_S), copies
  * or kernels already queued may still read h_keys/h_values or write h_out
  * afterwards. */

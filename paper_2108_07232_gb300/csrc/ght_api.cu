@@ -1201,28 +1201,24 @@ int ght_find_host(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out
   if (!h_queries || !h_out) return fail(GHT_ERR_INVALID_ARG, "queries or out is NULL");
   // Three-stage pipeline over chunks: H2D on one copy stream, find on the
   // table stream, D2H on a second copy stream (both link directions busy).
-  // Page-locked queries the device can address are read by the find kernel
-  // in place (no host-to-device copies; the first stage drops out).
-  const void *dq_view = nullptr;
-  const uint32_t *dq_host = device_view(h_queries, &dq_view) ? static_cast<const uint32_t *>(dq_view) : nullptr;
   uint32_t *d_buf = nullptr;
   cudaStream_t up = nullptr, down = nullptr;
   const uint64_t nchunks = (n + kChunk - 1) / kChunk;
   cudaEvent_t evs[8] = {};
   int rc = GHT_OK;
   bool h2d_started = false;  // the copy-span start event was recorded in this call
-  cudaError_t e = pool_alloc(reinterpret_cast<void **>(&d_buf), (dq_host ? 1 : 2) * n * sizeof(uint32_t), t->stream);
+  cudaError_t e = pool_alloc(reinterpret_cast<void **>(&d_buf), 2 * n * sizeof(uint32_t), t->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(GHT_ERR_OOM, "staging allocation: %s", cudaGetErrorString(e));
   }
-  uint32_t *d_q = dq_host ? nullptr : d_buf, *d_o = dq_host ? d_buf : d_buf + n;
+  uint32_t *d_q = d_buf, *d_o = d_buf + n;
   if ((e = cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking)) != cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking)) != cudaSuccess)
     rc = cuda_fail(e, "creating pipeline streams");
   for (int i = 0; rc == GHT_OK && i < 8; ++i)
     if ((e = cudaEventCreateWithFlags(&evs[i], cudaEventDisableTiming)) != cudaSuccess) rc = cuda_fail(e, "creating events");
-  if (rc == GHT_OK && !dq_host) {
+  if (rc == GHT_OK) {
     if ((e = cudaEventRecord(evs[0], t->stream)) != cudaSuccess || (e = cudaStreamWaitEvent(up, evs[0], 0)) != cudaSuccess)
       rc = cuda_fail(e, "ordering the staging copy");
     h2d_started = rc == GHT_OK && cudaEventRecord(t->tev[7], up) == cudaSuccess;
@@ -1232,13 +1228,12 @@ int ght_find_host(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out
   for (uint64_t i = 0; rc == GHT_OK && i < nchunks; ++i) {
     const uint64_t off = i * kChunk, len = std::min(kChunk, n - off);
     cudaEvent_t in = evs[i & 3], fin = evs[4 + (i & 3)];
-    if (!dq_host &&
-        ((e = cudaMemcpyAsync(d_q + off, h_queries + off, len * 4, cudaMemcpyHostToDevice, up)) != cudaSuccess ||
-         (e = cudaEventRecord(in, up)) != cudaSuccess || (e = cudaStreamWaitEvent(t->stream, in, 0)) != cudaSuccess)) {
+    if ((e = cudaMemcpyAsync(d_q + off, h_queries + off, len * 4, cudaMemcpyHostToDevice, up)) != cudaSuccess ||
+        (e = cudaEventRecord(in, up)) != cudaSuccess || (e = cudaStreamWaitEvent(t->stream, in, 0)) != cudaSuccess) {
       rc = cuda_fail(e, "staging queries");
       break;
     }
-    if ((e = launch_find(t, (dq_host ? dq_host : d_q) + off, d_o + off, len)) != cudaSuccess) {
+    if ((e = launch_find(t, d_q + off, d_o + off, len)) != cudaSuccess) {
       rc = cuda_fail(e, "launching find");
       break;
     }
@@ -1252,8 +1247,6 @@ int ght_find_host(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out
     cudaEventRecord(t->tev[8], up);
     t->timed_h2d = true;
     t->h2d_bytes = 4 * n;
-  } else if (dq_host) {
-    t->timed_h2d = false;  // queries read in place: no copies to time
   }
   if (rc == GHT_OK) {
     // the table stream frees the buffer after the last read-back

@@ -311,11 +311,11 @@ def test_build_in_place_from_pinned_host_memory(G, scheme, lf):
 @pytest.mark.parametrize("scheme,lf,nq", [("bcht", 0.99, (1 << 23) + 1001), ("p2bht", 0.8, 1 << 18),
                                           ("iht", 0.86, 1 << 18), ("cuckoo1", 0.5, 1 << 18),
                                           ("bcht_set", 0.99, 1 << 18), ("bcht_lb", 0.95, 1 << 18)])
-def test_find_in_place_from_pinned_host_memory(G, scheme, lf, nq):
-    """Page-locked host queries are read in place by the find kernels (no
-    host-to-device copies: last_h2d_ms is -1), pageable ones are staged by
-    copies; both answer as the definitional lookup does, over one chunk of
-    the host pipeline and over two (2^23 + 1001 queries)."""
+def test_find_from_pinned_and_pageable_host_memory(G, scheme, lf, nq):
+    """Host-buffer finds stage page-locked and pageable queries through the
+    chunked copy pipeline (the host-to-device copy span is recorded) and
+    answer as the definitional lookup does, over one chunk of the pipeline
+    and over two (2^23 + 1001 queries)."""
     n = (1 << 19) + 77
     keys, vals = W.make_keys(n, 71), W.make_values(n, 71)
     sets = scheme == "bcht_set"
@@ -330,8 +330,7 @@ def test_find_in_place_from_pinned_host_memory(G, scheme, lf, nq):
         got = t.find(qq)
         assert got.device.type == "cpu"
         assert (O._u32(got) == want).all(), src
-        copied = t.stats()["last_h2d_ms"] > 0
-        assert copied == (src == "pageable"), src
+        assert t.stats()["last_h2d_ms"] > 0, src
 
 
 def test_find_follows_the_current_stream(G):
