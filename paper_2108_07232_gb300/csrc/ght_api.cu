@@ -13,6 +13,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 #include <thread>
 
 #include "ght.h"
@@ -893,7 +894,29 @@ int build_device(ght_table *t, const uint32_t *k, const uint32_t *v, uint64_t n,
   return rc;
 }
 
-constexpr uint64_t kChunk = 1ull << 23;       // queries per host<->device pipeline chunk of a find
+// Chunks of a find's host<->device pipeline: from 2^20 queries doubling up
+// to 2^25 at the front and halving back down to 2^20 at the end, so the
+// copy-in before the first find and the copy-out after the last are short
+// and the middle runs few, long launches.
+constexpr uint64_t kChunkFirst = 1ull << 20, kChunkCap = 1ull << 25;
+
+std::vector<uint64_t> find_chunks(uint64_t n) {
+  std::vector<uint64_t> head, mid;
+  uint64_t left = n;
+  for (uint64_t c = kChunkFirst; c < kChunkCap && left >= 2 * c; c *= 2) {
+    head.push_back(c);
+    left -= 2 * c;
+  }
+  while (left > 0) {
+    const uint64_t c = std::min(left, kChunkCap);
+    mid.push_back(c);
+    left -= c;
+  }
+  std::vector<uint64_t> plan(head);
+  plan.insert(plan.end(), mid.begin(), mid.end());
+  plan.insert(plan.end(), head.rbegin(), head.rend());
+  return plan;
+}
 constexpr uint64_t kBuildChunk = 1ull << 25;  // pairs per chunk of a host-buffer build (fewer insert launch tails)
 
 // check_duplicates: after a successful build from device keys, no key may be
@@ -1203,7 +1226,7 @@ int ght_find_host(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out
   // table stream, D2H on a second copy stream (both link directions busy).
   uint32_t *d_buf = nullptr;
   cudaStream_t up = nullptr, down = nullptr;
-  const uint64_t nchunks = (n + kChunk - 1) / kChunk;
+  const std::vector<uint64_t> chunks = find_chunks(n);
   cudaEvent_t evs[8] = {};
   int rc = GHT_OK;
   bool h2d_started = false;  // the copy-span start event was recorded in this call
@@ -1225,8 +1248,9 @@ int ght_find_host(const ght_table *t, const uint32_t *h_queries, uint32_t *h_out
   }
   // events 0..3: "chunk landed" ring; 4..7: "chunk answered" ring. Reusing an
   // event is safe because each stream consumes them in order.
-  for (uint64_t i = 0; rc == GHT_OK && i < nchunks; ++i) {
-    const uint64_t off = i * kChunk, len = std::min(kChunk, n - off);
+  uint64_t off = 0;
+  for (uint64_t i = 0; rc == GHT_OK && i < chunks.size(); off += chunks[i], ++i) {
+    const uint64_t len = chunks[i];
     cudaEvent_t in = evs[i & 3], fin = evs[4 + (i & 3)];
     if ((e = cudaMemcpyAsync(d_q + off, h_queries + off, len * 4, cudaMemcpyHostToDevice, up)) != cudaSuccess ||
         (e = cudaEventRecord(in, up)) != cudaSuccess || (e = cudaStreamWaitEvent(t->stream, in, 0)) != cudaSuccess) {
